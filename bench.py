@@ -1,0 +1,357 @@
+"""Benchmark of the B300 acoustic FD propagator (one JSON line on stdout).
+
+Workload: the layered 3D single-shot stencil, 512^3 FP32 grid, radius-4
+Laplacian, 20-point sponge on all faces, 10 Hz Ricker source near the top,
+256 x 256 receivers, 1000 time steps.  One benchmark step is one whole shot
+(1000 fused time-step launches plus the receiver gathers), run through the C
+ABI (fd_run_shot) on device-resident inputs.  The fields (3 x 537 MB) are
+larger than the 126 MB L2, so every time step streams from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own shot on its own GPU (independent
+replicas, weak scaling, no data-path collective); the barrier and the max over
+ranks of the timed region are the only collectives.
+
+Reported beside the device-timed value: ``e2e`` (the same metric with the
+velocity uploaded from pinned host memory and the traces read back every
+step), ``roofline`` (the step kernel's algorithmic HBM bytes per launch over
+its average launch time, against the measured copy bandwidth), ``clocks``
+(nvidia-smi sampled during the timed region) and ``cpu_baseline`` (the FP64
+oracle on the host cores, on a bounded sample of the same grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+BYTES_PER_UPDATE = 16          # read P, Pold, w; write Pn (FP32)
+FALLBACK_HBM_GBS = 6400.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fd_step3d_512cube_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2311_05038_b300", "csrc", f)
+                  for f in ("fd_kernels.cu", "fd_internal.h", "ptx.cuh")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="cube side")
+    ap.add_argument("--nt", type=int, default=1000, help="time steps per shot")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------ helpers
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, scaled to n^3,
+    or None if the summary is missing or the kernel source changed since."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_digest():
+            return None
+        per_point = float(kv["dram_bytes_per_launch"]) / float(kv["points_per_launch"])
+        return per_point * n ** 3
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling for the duration of a with-block."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id, enabled=True):
+        self.gpu_id = gpu_id
+        self.enabled = enabled
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                time.sleep(0.3)
+            except Exception:
+                self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [s for s in sm if smax and s > 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "b300" else "gloo")
+        return dist, rank, local, world
+    return None, 0, 0, 1
+
+
+# ------------------------------------------------------------------------ oracle
+
+def oracle_sample(shot, budget_s=15.0, max_steps=50):
+    """Time the FP64 oracle on the benchmark grid for a bounded number of steps."""
+    from oracle import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    P, Pold, _ = oracle.run(3, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width,
+                            src=shot.src, wavelet=shot.wavelet, receivers=None, nsteps=1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(3, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width, src=shot.src,
+               wavelet=shot.wavelet, receivers=shot.receivers, P=P, Pold=Pold, n0=1, nsteps=steps)
+    el = time.perf_counter() - t0
+    return steps * shot.npoints / el / 1e9, threads, steps, el
+
+
+def run_reference(args, dist, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, same grid and metric."""
+    if rank != 0:
+        return
+    shot = wl.roofline_3d(n=args.n, nt=args.nt)
+    from oracle import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    # size one benchmark step from a one-time-step probe (about 8 s of CPU work)
+    t0 = time.perf_counter()
+    P, Pold, _ = oracle.run(3, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width,
+                            src=shot.src, wavelet=shot.wavelet, nsteps=1)
+    probe = time.perf_counter() - t0
+    per_step = int(max(1, min(args.nt, 8.0 / max(probe, 1e-3))))
+    n0 = 1
+
+    def one():
+        nonlocal P, Pold, n0
+        P, Pold, _ = oracle.run(3, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width,
+                                src=shot.src, wavelet=shot.wavelet, receivers=shot.receivers,
+                                P=P, Pold=Pold, n0=n0, nsteps=per_step)
+        n0 += per_step
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    value = args.steps * per_step * shot.npoints / el / 1e9
+    sample = (f"{args.n}^3 layered grid, {per_step} of {args.nt} time steps per benchmark step, "
+              f"FP64 oracle (plain C loop, OpenMP over z)")
+    line = {
+        "impl": "reference", "metric": "Gpt-updates/s", "value": value, "unit": "Gupd/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": shot.name, "grid": list(shot.shape), "time_steps_per_bench_step": per_step,
+                   "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "Gupd/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gupd/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ main arm
+
+def run_b300(args, dist, rank, local, world):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2311_05038_b300 import fd
+
+    shot = wl.roofline_3d(n=args.n, nt=args.nt)
+    npts = shot.npoints
+    stream = torch.cuda.Stream()
+    model = fd.Model.from_shot(shot, stream=stream)
+    nrec = len(shot.receivers)
+    traces = torch.empty((shot.nt, nrec), device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident timed region
+    for _ in range(args.warmup):
+        model.run_shot(shot.nt, traces)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else local
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = fd.fd_kernel_launch_count()
+    with ClockSampler(gpu_id, enabled=not args.no_clocks) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            model.run_shot(shot.nt, traces)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = fd.fd_kernel_launch_count() - launches0
+    fd.fd_synchronize(model.handle)
+    barrier()
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    value = world * args.steps * shot.nt * npts / elapsed / 1e9
+    step_launches = args.steps * shot.nt
+    avg_launch_s = ev0.elapsed_time(ev1) / 1e3 / step_launches
+    achieved = BYTES_PER_UPDATE * npts / avg_launch_s / 1e9
+    peak, peak_kind = measured_hbm_peak()
+
+    # ---- end to end: velocity up from pinned host memory, traces back, every step
+    e2e = None
+    if not args.skip_e2e:
+        v_pinned = torch.from_numpy(shot.vel.ravel()).pin_memory()
+        tr_pinned = torch.empty((shot.nt, nrec), dtype=torch.float32).pin_memory()
+        rec = shot.receivers
+
+        def e2e_step():
+            fd.fd_set_velocity_ptr(model.handle, v_pinned.data_ptr())
+            model.set_source(shot.src, shot.wavelet)
+            model.set_receivers(rec)
+            model.run_shot(shot.nt)
+            fd.fd_gather_traces_ptr(model.handle, tr_pinned.data_ptr(), tr_pinned.numel())
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        h2d = shot.vel.nbytes + shot.wavelet.nbytes + rec.nbytes
+        d2h = shot.nt * nrec * 4
+        e2e = {"value": world * args.steps * shot.nt * npts / el / 1e9, "unit": "Gupd/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    model.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        del traces
+        torch.cuda.empty_cache()
+        v, threads, steps, el = oracle_sample(shot)
+        cpu = {"value": v, "unit": "Gupd/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.n}^3 layered grid with sponge, source and receivers, {steps} of "
+                         f"{args.nt} time steps, FP64 oracle, {el:.1f} s"}
+
+    if rank == 0:
+        traffic = recorded_traffic(args.n)
+        line = {
+            "metric": "Gpt-updates/s", "value": value, "unit": "Gupd/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": shot.name, "grid": list(shot.shape), "time_steps_per_bench_step": shot.nt,
+                       "receivers": nrec, "sponge": shot.sponge_width,
+                       "l2": "fields (3 x %.0f MB) larger than L2; no flush needed" % (npts * 4 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic, "kernel": "fdk::step3d_kernel",
+                         "algorithmic_bytes_per_launch": BYTES_PER_UPDATE * npts,
+                         "avg_launch_us": avg_launch_s * 1e6},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks.summary(),
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist, rank, local, world = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, rank, world)
+        else:
+            run_b300(args, dist, rank, local, world)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * fd.h -- C ABI of the B300 acoustic finite-difference propagator (libfd).
+ *
+ * The library advances the acoustic wave equation of the paper's proof of
+ * concept (section 7, Eq. 1),
+ *
+ *     P_tt = v(x)^2 (P_xx + P_zz [+ P_yy]) + S(t) delta(x - x_s),
+ *
+ * with the routine sequence of its WaveSimulator::run() listing (add_source,
+ * fd_pzz, fd_pxx, fd_time, then the two swaps), fused into one CUDA kernel per
+ * time step on an sm_103a GPU.  One step maps the levels (P, Pold) at t_n,
+ * t_{n-1} to Pn at t_{n+1}:
+ *
+ *     L'P  = sum_{k=1..4} c_k ( S_k - 2d P ),   S_k = sum over the d axes of
+ *            P[i + k e] + P[i - k e],   c = (8/5, -1/5, 8/315, -1/560)
+ *            (the radius-4 Taylor stencil; P = 0 outside the grid)
+ *     Pn   = ( 2P - (1 - a) Pold + w L'P ) / (1 + a),   w = (dt v / h)^2,
+ *            a = dt (eta_x(ix) + eta_y(iy) + eta_z(iz))   (sponge; a = 0 inside)
+ *     Pn[src] += dt^2 S(t_n) / h^d                        (add_source)
+ *     trace[n][r] = Pn[rec_r]                             (receivers, at t_{n+1})
+ *     Pold <- P, P <- Pn                                  (the swaps)
+ *
+ * The sponge profile of each axis is eta_max (d / W)^2 for a point d =
+ * max(W - i, i - (n - 1 - W), 0) points into a W-point band, with
+ * eta_max = 3 v_max ln(1/R) / (2 W h).  The stencil order, boundary, sponge,
+ * source scaling and receivers are not fixed by the paper; these are the
+ * readings this library implements.
+ *
+ * Following the paper's start/stop convention (section 5), every input is
+ * built on the host and copied in by the library ("copyFromHost"), and every
+ * output leaves through an explicit gather call ("copyToHost").  The *_dev
+ * variants take device pointers instead, for callers that keep data on the
+ * GPU (e.g. PyTorch tensors); the library never takes ownership of them.
+ *
+ * Layout: every field is x-fastest, [nz][ny][nx] in 3D and [nz][nx] in 2D
+ * (ny = 1), FP32.  Points are (ix, iy, iz) with iy = 0 in 2D.
+ *
+ * Errors: every entry point returns an fd_status; 0 is success, negative
+ * values are errors.  No entry point aborts or throws; fd_last_error() gives a
+ * message for the calling thread's last failure.  On a validation error
+ * nothing is modified.
+ *
+ * Threading: a model is used from one host thread at a time; all its GPU work
+ * is ordered on the stream given at creation.  Different models are
+ * independent.
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fd_status;
+
+#define FD_OK        0
+#define FD_EINVAL   (-1)  /* bad dimensions, NULL pointer, bad size or count      */
+#define FD_ECFL     (-2)  /* v_max dt / h above the leapfrog stability limit       */
+#define FD_ERANGE   (-3)  /* source or receiver outside the grid                   */
+#define FD_ENOMEM   (-4)  /* device allocation failed                              */
+#define FD_EBUDGET  (-5)  /* request exceeds a caller-stated memory budget         */
+#define FD_ECUDA    (-6)  /* a CUDA call failed (no device, launch error, ...)     */
+#define FD_ETIMEOUT (-7)  /* a bounded device-side wait gave up                    */
+#define FD_ESTATE   (-8)  /* call not valid in the model's current state           */
+
+typedef struct fd_model fd_model;   /* opaque; owns its device wavefields */
+
+/* Grid and discretisation of one model. */
+typedef struct fd_grid_desc {
+    int ndim;           /* 2 or 3                                                */
+    int nx, ny, nz;     /* extents >= 1; ny must be 1 when ndim == 2             */
+    double h;           /* grid spacing (m), > 0, the same on every axis         */
+    double dt;          /* time step (s), > 0                                    */
+    int sponge_width;   /* W >= 0 points of damping band on every face           */
+    double sponge_R;    /* target reflection coefficient in (0, 1); used if W > 0 */
+} fd_grid_desc;
+
+/* Stability limit of the Courant number v_max dt / h for ndim = 2 or 3:
+ * 2 / sqrt(ndim lambda_1), lambda_1 = -(c_0 + 2 sum_k (-1)^k c_k) of the
+ * radius-4 stencil (the leapfrog condition omega dt <= 2).  Returns a negative
+ * value for any other ndim. */
+double fd_cfl_limit(int ndim);
+
+/* The FP32 stencil weights c_1..c_4 the kernels use (host memory, 4 floats). */
+fd_status fd_stencil_weights(float *out4);
+
+/* Create a model: allocates the device fields P, Pold, w = (dt v / h)^2 and
+ * the sponge profiles, computes w and the profiles on the device from the
+ * velocity (m/s, [nz][ny][nx], copied), and sets P = Pold = 0, n = 0.
+ * stream: a cudaStream_t (NULL = the legacy default stream) on which all of the
+ * model's GPU work is ordered; the caller keeps it alive until destroy.
+ * Errors: FD_EINVAL (bad desc, NULL pointers, non-positive or non-finite
+ * velocity), FD_ECFL (v_max dt / h > fd_cfl_limit(ndim)), FD_ENOMEM, FD_ECUDA.
+ * On success *out owns the device memory until fd_model_destroy. */
+fd_status fd_model_create(const fd_grid_desc *desc, const float *v_host, void *stream,
+                          fd_model **out);
+/* As fd_model_create, but v_dev is a device pointer (dense [nz][ny][nx]). */
+fd_status fd_model_create_dev(const fd_grid_desc *desc, const float *v_dev, void *stream,
+                              fd_model **out);
+
+/* Release everything the model owns (waits for its stream first).  NULL is a no-op. */
+fd_status fd_model_destroy(fd_model *m);
+
+/* Replace the velocity model (same grid and dt); recomputes w and the sponge.
+ * Same checks as create (FD_EINVAL, FD_ECFL).  Does not touch P, Pold or n. */
+fd_status fd_set_velocity(fd_model *m, const float *v_host);
+fd_status fd_set_velocity_dev(fd_model *m, const float *v_dev);
+
+/* Point source at (ix, iy, iz) with signature S(t_n) = wavelet[n], n < nt
+ * (host, copied; steps n >= nt inject nothing).  nt = 0 or wavelet = NULL
+ * removes the source.  FD_ERANGE if the point is outside the grid. */
+fd_status fd_set_source(fd_model *m, int ix, int iy, int iz, const float *wavelet_host, int nt);
+
+/* Receivers at nrec points given as (ix, iy, iz) int triples (host, copied).
+ * nrec = 0 removes them.  FD_ERANGE if any point is outside the grid. */
+fd_status fd_set_receivers(fd_model *m, const int *xyz_host, int nrec);
+
+/* Trace buffer for the next steps: [nt_rows][nrec] FP32 on the device.  If
+ * traces_dev is NULL the library allocates (and owns) it, else it writes into
+ * the caller's buffer, which must stay valid while steps run.  Step n writes
+ * row n (the model's step counter) when n < nt_rows. */
+fd_status fd_set_trace_buffer(fd_model *m, float *traces_dev, int nt_rows);
+
+/* P = Pold = 0 and step counter n = 0.  Source, receivers, traces kept. */
+fd_status fd_reset(fd_model *m);
+
+/* Set the state: P (level n) and Pold (level n-1), dense host arrays, and the
+ * step counter n >= 0 (checkpoint resume / initial conditions). */
+fd_status fd_set_wavefield(fd_model *m, const float *p_host, const float *pold_host, int n);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the model's stream. */
+fd_status fd_step(fd_model *m, int nsteps);
+
+/* One shot: reset, record into traces_dev ([nt][nrec] device buffer, or NULL
+ * for a library-owned buffer), advance nt steps.  Asynchronous. */
+fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev);
+
+/* Copy the recorded traces [rows][nrec] to host memory (cap = floats available;
+ * FD_EINVAL if smaller than rows * nrec).  Synchronises the model's stream. */
+fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap);
+
+/* Copy P (level n) and, if pold_host is not NULL, Pold (level n-1) to dense
+ * host arrays of cap floats each.  Synchronises the model's stream. */
+fd_status fd_get_wavefield(fd_model *m, float *p_host, float *pold_host, size_t cap);
+
+/* Wait for the model's stream; reports a device-side error flag if any kernel
+ * raised one (FD_ETIMEOUT for a bounded wait that gave up). */
+fd_status fd_synchronize(fd_model *m);
+
+/* Introspection (host outputs): the step counter; the linear indices
+ * (iz*ny + iy)*nx + ix of the source (-1 if none) and of each receiver; the
+ * per-axis damping a = dt * eta as the kernels use it (axis 0 = x, 1 = y,
+ * 2 = z; n_axis floats). */
+fd_status fd_get_step(fd_model *m, int *n);
+fd_status fd_get_source_index(fd_model *m, int64_t *idx);
+fd_status fd_get_receiver_indices(fd_model *m, int64_t *out, int cap);
+fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
+
+/* Number of CUDA kernel launches this library has issued since load. */
+uint64_t fd_kernel_launch_count(void);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *fd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_H */

@@ -1,0 +1,747 @@
+// fd_api.cu -- host side of the C ABI declared in include/fd.h.
+//
+// The model object plays the role of the paper's WaveSimulator (section 7,
+// Listing 3): it owns the wavefields P and Pold, the velocity-derived w and the
+// time step, and its fd_step() runs the routine sequence of run() -- here one
+// fused kernel launch per time step, followed by the pointer swaps.  Inputs
+// enter only through copying calls and outputs leave only through gather
+// calls, the start/stop convention of section 5.
+//
+// Device layout: every field is [nz][ny][px] FP32 with a row pitch px = nx
+// rounded up to 32 elements (128-byte rows, as TMA needs 16-byte strides).
+// Columns past nx are never read by the stencil (the tensor maps stop at nx and
+// zero-fill beyond), so the pitch is invisible to callers.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "fd.h"
+#include "fd_internal.h"
+
+using namespace fdk;
+
+// ------------------------------------------------------------------ errors & stats
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+static fd_status fail(fd_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static fd_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(FD_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FD_CUDA(call, what)                 \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess)              \
+            return cuda_fail(e_, what);     \
+    } while (0)
+
+// --------------------------------------------------------------- stencil weights
+
+// Weights of the radius-4 centred second difference from Fornberg's closed
+// form c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!), evaluated in FP64.
+static double weight(int k)
+{
+    const int r = kRadius;
+    double f[2 * kRadius + 1];
+    f[0] = 1.0;
+    for (int i = 1; i <= 2 * r; ++i)
+        f[i] = f[i - 1] * i;
+    const double sign = (k % 2 == 1) ? 1.0 : -1.0;
+    return 2.0 * sign * f[r] * f[r] / ((double)k * k * f[r - k] * f[r + k]);
+}
+
+extern "C" double fd_cfl_limit(int ndim)
+{
+    if (ndim != 2 && ndim != 3)
+        return -1.0;
+    // lambda_1 = -(c_0 + 2 sum_k (-1)^k c_k) with c_0 = -2 sum_k c_k
+    double sum = 0.0, alt = 0.0;
+    for (int k = 1; k <= kRadius; ++k) {
+        sum += weight(k);
+        alt += ((k % 2) ? -1.0 : 1.0) * weight(k);
+    }
+    const double lambda1 = -(-2.0 * sum + 2.0 * alt);
+    return 2.0 / std::sqrt(ndim * lambda1);
+}
+
+extern "C" fd_status fd_stencil_weights(float *out4)
+{
+    if (!out4)
+        return fail(FD_EINVAL, "fd_stencil_weights: NULL output");
+    for (int k = 1; k <= kRadius; ++k)
+        out4[k - 1] = (float)weight(k);
+    return FD_OK;
+}
+
+// ------------------------------------------------------------------ tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// FP32 tensor map over a pitched field: rank 2 ([nz][px], extents nx, nz) or
+// rank 3 ([nz][ny][px], extents nx, ny, nz), with the given box.
+static bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t dims[3];
+    cuuint64_t strides[2];
+    cuuint32_t box[3];
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint32_t rank;
+    if (ndim == 2) {
+        rank = 2;
+        dims[0] = nx;
+        dims[1] = nz;
+        strides[0] = (cuuint64_t)px * 4;
+        box[0] = bx;
+        box[1] = by;
+    } else {
+        rank = 3;
+        dims[0] = nx;
+        dims[1] = ny;
+        dims[2] = nz;
+        strides[0] = (cuuint64_t)px * 4;
+        strides[1] = (cuuint64_t)px * ny * 4;
+        box[0] = bx;
+        box[1] = by;
+        box[2] = 1;
+    }
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------------ model
+
+struct fd_model {
+    fd_grid_desc d{};
+    int nx = 0, ny = 0, nz = 0, px = 0;
+    size_t rows = 0;       // nz * ny
+    size_t pitched = 0;    // rows * px elements per field
+    size_t npts = 0;       // nz * ny * nx
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    float *buf[2] = {nullptr, nullptr};   // the two wavefield levels
+    int cur = 0;                          // buf[cur] = P, buf[cur ^ 1] = Pold
+    float *w = nullptr;
+    float *ax = nullptr, *ay = nullptr, *az = nullptr;
+    int has_sponge = 0;
+    float vmax = 0.f;
+    int *d_err = nullptr;
+    unsigned *d_stats = nullptr;
+
+    CUtensorMap halo_map[2];   // haloed P box over buf[i]
+    CUtensorMap tile_map[2];   // unhaloed box over buf[i] (as Pold)
+    CUtensorMap w_map;
+    int nchunks = 1;           // 3D: CTAs along z
+    int bz = 1;
+
+    int src_on = 0, sx = 0, sy = 0, sz = 0;
+    std::vector<float> amp;    // dt^2 S(t_n) / h^d
+
+    int nrec = 0;
+    int64_t *d_rec = nullptr;  // pitched indices (device)
+    int rec_cap = 0;
+    std::vector<int64_t> rec_dense;
+
+    float *traces = nullptr;
+    int trace_rows = 0;
+    bool traces_owned = false;
+    size_t trace_cap = 0;      // floats in an owned trace buffer
+    float *stage = nullptr;    // velocity staging, kept once fd_set_velocity is used
+
+    int n = 0;
+    int pending_row = -1;      // receiver row whose gather is still owed
+};
+
+static fd_status validate_desc(const fd_grid_desc *d)
+{
+    if (!d)
+        return fail(FD_EINVAL, "NULL grid descriptor");
+    if (d->ndim != 2 && d->ndim != 3)
+        return fail(FD_EINVAL, "ndim must be 2 or 3 (got %d)", d->ndim);
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+        return fail(FD_EINVAL, "grid extents must be >= 1 (got %d x %d x %d)", d->nx, d->ny, d->nz);
+    if (d->ndim == 2 && d->ny != 1)
+        return fail(FD_EINVAL, "2D grids need ny == 1 (got %d)", d->ny);
+    if (!(d->h > 0.0) || !std::isfinite(d->h) || !(d->dt > 0.0) || !std::isfinite(d->dt))
+        return fail(FD_EINVAL, "h and dt must be positive and finite");
+    if (d->sponge_width < 0)
+        return fail(FD_EINVAL, "sponge_width must be >= 0");
+    if (d->sponge_width > 0 && !(d->sponge_R > 0.0 && d->sponge_R < 1.0))
+        return fail(FD_EINVAL, "sponge_R must lie in (0, 1)");
+    const double npts = (double)d->nx * d->ny * d->nz;
+    if (npts > 4.0e10)
+        return fail(FD_EINVAL, "grid of %.3g points is too large", npts);
+    return FD_OK;
+}
+
+// Per-axis damping a_i = dt * eta_max * (d_i / W)^2, d_i = max(W - i, i - (n-1-W), 0).
+static std::vector<float> damping_profile(int n, int len, int W, double eta_max, double dt)
+{
+    std::vector<float> a(len, 0.f);
+    if (W <= 0)
+        return a;
+    for (int i = 0; i < n; ++i) {
+        const int d = std::max(std::max(W - i, i - (n - 1 - W)), 0);
+        const double r = (double)d / W;
+        a[i] = (float)(dt * eta_max * r * r);
+    }
+    return a;
+}
+
+static void free_model(fd_model *m)
+{
+    if (!m)
+        return;
+    cudaFree(m->buf[0]);
+    cudaFree(m->buf[1]);
+    cudaFree(m->w);
+    cudaFree(m->ax);
+    cudaFree(m->ay);
+    cudaFree(m->az);
+    cudaFree(m->d_err);
+    cudaFree(m->d_stats);
+    cudaFree(m->d_rec);
+    cudaFree(m->stage);
+    if (m->traces_owned)
+        cudaFree(m->traces);
+    delete m;
+}
+
+// Load a dense velocity (host or device) into a staging copy, check it, and on
+// success turn it into w and the sponge profiles.  Leaves the model untouched
+// on failure.
+static fd_status load_velocity(fd_model *m, const float *v, cudaMemcpyKind kind)
+{
+    if (!v)
+        return fail(FD_EINVAL, "NULL velocity");
+    if (!m->stage)
+        FD_CUDA(cudaMalloc((void **)&m->stage, m->pitched * sizeof(float)), "staging allocation");
+    float *stage = m->stage;
+    cudaError_t e = cudaMemcpy2DAsync(stage, (size_t)m->px * 4, v, (size_t)m->nx * 4, (size_t)m->nx * 4, m->rows,
+                                      kind, m->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(m->d_stats, 0, 2 * sizeof(unsigned), m->stream);
+    if (e == cudaSuccess) {
+        e = launch_velocity_stats(stage, m->nx, m->rows, m->px, m->d_stats, m->stream);
+        ++g_launches;
+    }
+    unsigned stats[2] = {0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(stats, m->d_stats, sizeof stats, cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        return cuda_fail(e, "velocity upload");
+    }
+    if (stats[1] != 0) {
+        return fail(FD_EINVAL, "velocity has %u entries that are not finite and positive", stats[1]);
+    }
+    float vmax;
+    std::memcpy(&vmax, &stats[0], sizeof vmax);
+    const double courant = (double)vmax * m->d.dt / m->d.h;
+    const double lim = fd_cfl_limit(m->d.ndim);
+    if (courant > lim) {
+        return fail(FD_ECFL, "Courant number v_max dt / h = %.6g exceeds the stability limit %.6g", courant, lim);
+    }
+    e = launch_compute_w(stage, m->w, m->nx, m->rows, m->px, m->d.dt / m->d.h, m->stream);
+    ++g_launches;
+    if (e != cudaSuccess) {
+        return cuda_fail(e, "computing w");
+    }
+    m->vmax = vmax;
+    const int W = m->d.sponge_width;
+    m->has_sponge = W > 0;
+    const double eta_max = W > 0 ? 3.0 * (double)vmax * std::log(1.0 / m->d.sponge_R) / (2.0 * W * m->d.h) : 0.0;
+    auto pax = damping_profile(m->nx, m->px, W, eta_max, m->d.dt);
+    auto pay = damping_profile(m->ny, m->ny, m->d.ndim == 3 ? W : 0, eta_max, m->d.dt);
+    auto paz = damping_profile(m->nz, m->nz, W, eta_max, m->d.dt);
+    FD_CUDA(cudaMemcpyAsync(m->ax, pax.data(), pax.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge x");
+    FD_CUDA(cudaMemcpyAsync(m->ay, pay.data(), pay.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge y");
+    FD_CUDA(cudaMemcpyAsync(m->az, paz.data(), paz.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge z");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "velocity setup");
+    return FD_OK;
+}
+
+static fd_status create(const fd_grid_desc *desc, const float *v, cudaMemcpyKind kind, void *stream,
+                        fd_model **out)
+{
+    if (!out)
+        return fail(FD_EINVAL, "NULL output pointer");
+    *out = nullptr;
+    fd_status st = validate_desc(desc);
+    if (st)
+        return st;
+    if (!v)
+        return fail(FD_EINVAL, "NULL velocity");
+    if (kind == cudaMemcpyHostToDevice) {
+        // Host input: reject a bad model or an unstable time step before
+        // touching the device (the device-side check repeats this).
+        const size_t n = (size_t)desc->nx * desc->ny * desc->nz;
+        float vmax = 0.f;
+        size_t bad = 0;
+        for (size_t i = 0; i < n; ++i) {
+            const float x = v[i];
+            if (std::isfinite(x) && x > 0.f)
+                vmax = std::max(vmax, x);
+            else
+                ++bad;
+        }
+        if (bad)
+            return fail(FD_EINVAL, "velocity has %zu entries that are not finite and positive", bad);
+        const double courant = (double)vmax * desc->dt / desc->h;
+        if (courant > fd_cfl_limit(desc->ndim))
+            return fail(FD_ECFL, "Courant number v_max dt / h = %.6g exceeds the stability limit %.6g", courant,
+                        fd_cfl_limit(desc->ndim));
+    }
+
+    fd_model *m = new fd_model();
+    m->d = *desc;
+    m->nx = desc->nx;
+    m->ny = desc->ny;
+    m->nz = desc->nz;
+    m->px = (desc->nx + 31) / 32 * 32;
+    m->rows = (size_t)m->nz * m->ny;
+    m->pitched = m->rows * m->px;
+    m->npts = m->rows * m->nx;
+    m->stream = static_cast<cudaStream_t>(stream);
+
+    auto bail = [&](fd_status s) {
+        free_model(m);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess)
+        return bail(cuda_fail(e, "cudaGetDevice"));
+    const size_t bytes = m->pitched * sizeof(float);
+    if ((e = cudaMalloc((void **)&m->buf[0], bytes)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->buf[1], bytes)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->w, bytes)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->ax, (size_t)m->px * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->ay, (size_t)m->ny * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->az, (size_t)m->nz * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->d_stats, 2 * sizeof(unsigned))) != cudaSuccess)
+        return bail(cuda_fail(e, "device allocation"));
+    if ((e = cudaMemsetAsync(m->buf[0], 0, bytes, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->buf[1], 0, bytes, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->w, 0, bytes, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "device memset"));
+
+    st = load_velocity(m, v, kind);
+    if (st)
+        return bail(st);
+    // the staging copy is kept only by models whose velocity is replaced later
+    cudaFree(m->stage);
+    m->stage = nullptr;
+
+    const int ndim = desc->ndim;
+    bool ok = true;
+    for (int i = 0; i < 2; ++i) {
+        if (ndim == 3) {
+            ok = ok && make_map(&m->halo_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3 + 8, kTY3 + 8);
+            ok = ok && make_map(&m->tile_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3);
+        } else {
+            ok = ok && make_map(&m->halo_map[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, kTX2 + 8, kTZ2 + 8);
+            ok = ok && make_map(&m->tile_map[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, kTX2, kTZ2);
+        }
+    }
+    ok = ok && (ndim == 3 ? make_map(&m->w_map, m->w, 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3)
+                          : make_map(&m->w_map, m->w, 2, m->nx, 1, m->nz, m->px, kTX2, kTZ2));
+    if (!ok)
+        return bail(fail(FD_ECUDA, "cuTensorMapEncodeTiled failed"));
+
+    if (ndim == 3) {
+        if ((e = step3d_prepare()) != cudaSuccess)
+            return bail(cuda_fail(e, "kernel attributes"));
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+        const long long tiles = (long long)((m->nx + kTX3 - 1) / kTX3) * ((m->ny + kTY3 - 1) / kTY3);
+        const long long slots = (long long)sms * step3d_blocks_per_sm();
+        // About six waves of CTAs, each marching at least 32 planes.
+        long long bz = (long long)m->nz * tiles / (6 * slots);
+        bz = std::max(32LL, std::min<long long>(bz, m->nz));
+        m->nchunks = (int)((m->nz + bz - 1) / bz);
+        m->bz = (m->nz + m->nchunks - 1) / m->nchunks;
+    }
+    *out = m;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_model_create(const fd_grid_desc *desc, const float *v_host, void *stream, fd_model **out)
+{
+    return create(desc, v_host, cudaMemcpyHostToDevice, stream, out);
+}
+
+extern "C" fd_status fd_model_create_dev(const fd_grid_desc *desc, const float *v_dev, void *stream,
+                                         fd_model **out)
+{
+    return create(desc, v_dev, cudaMemcpyDeviceToDevice, stream, out);
+}
+
+extern "C" fd_status fd_model_destroy(fd_model *m)
+{
+    if (!m)
+        return FD_OK;
+    cudaSetDevice(m->device);
+    cudaStreamSynchronize(m->stream);
+    free_model(m);
+    return FD_OK;
+}
+
+#define NEED_MODEL(m)                                              \
+    do {                                                           \
+        if (!(m))                                                  \
+            return fail(FD_EINVAL, "NULL model");                  \
+        cudaError_t e_ = cudaSetDevice((m)->device);               \
+        if (e_ != cudaSuccess)                                     \
+            return cuda_fail(e_, "cudaSetDevice");                 \
+    } while (0)
+
+extern "C" fd_status fd_set_velocity(fd_model *m, const float *v_host)
+{
+    NEED_MODEL(m);
+    return load_velocity(m, v_host, cudaMemcpyHostToDevice);
+}
+
+extern "C" fd_status fd_set_velocity_dev(fd_model *m, const float *v_dev)
+{
+    NEED_MODEL(m);
+    return load_velocity(m, v_dev, cudaMemcpyDeviceToDevice);
+}
+
+static bool inside(const fd_model *m, int ix, int iy, int iz)
+{
+    return ix >= 0 && ix < m->nx && iy >= 0 && iy < m->ny && iz >= 0 && iz < m->nz;
+}
+
+extern "C" fd_status fd_set_source(fd_model *m, int ix, int iy, int iz, const float *wavelet_host, int nt)
+{
+    if (!m)
+        return fail(FD_EINVAL, "NULL model");
+    if (nt < 0)
+        return fail(FD_EINVAL, "nt must be >= 0");
+    if (m->d.ndim == 2)
+        iy = 0;
+    if (nt == 0 || !wavelet_host) {
+        m->src_on = 0;
+        m->amp.clear();
+        return FD_OK;
+    }
+    if (!inside(m, ix, iy, iz))
+        return fail(FD_ERANGE, "source (%d, %d, %d) outside the %d x %d x %d grid", ix, iy, iz, m->nx, m->ny, m->nz);
+    const double hd = m->d.ndim == 3 ? m->d.h * m->d.h * m->d.h : m->d.h * m->d.h;
+    std::vector<float> amp(nt);
+    for (int i = 0; i < nt; ++i)
+        amp[i] = (float)(m->d.dt * m->d.dt * (double)wavelet_host[i] / hd);
+    m->amp.swap(amp);
+    m->src_on = 1;
+    m->sx = ix;
+    m->sy = iy;
+    m->sz = iz;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_set_receivers(fd_model *m, const int *xyz_host, int nrec)
+{
+    NEED_MODEL(m);
+    if (nrec < 0 || (nrec > 0 && !xyz_host))
+        return fail(FD_EINVAL, "bad receiver list");
+    std::vector<int64_t> pit(nrec), dense(nrec);
+    for (int r = 0; r < nrec; ++r) {
+        const int ix = xyz_host[3 * r], iy = m->d.ndim == 3 ? xyz_host[3 * r + 1] : 0, iz = xyz_host[3 * r + 2];
+        if (!inside(m, ix, iy, iz))
+            return fail(FD_ERANGE, "receiver %d at (%d, %d, %d) outside the grid", r, ix, iy, iz);
+        pit[r] = ((int64_t)iz * m->ny + iy) * m->px + ix;
+        dense[r] = ((int64_t)iz * m->ny + iy) * m->nx + ix;
+    }
+    if (nrec > m->rec_cap) {
+        int64_t *p = nullptr;
+        FD_CUDA(cudaMalloc((void **)&p, (size_t)nrec * sizeof(int64_t)), "receiver allocation");
+        cudaStreamSynchronize(m->stream);
+        cudaFree(m->d_rec);
+        m->d_rec = p;
+        m->rec_cap = nrec;
+    }
+    if (nrec > 0)
+        FD_CUDA(cudaMemcpyAsync(m->d_rec, pit.data(), (size_t)nrec * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                m->stream),
+                "receiver upload");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "receiver upload");
+    if (nrec != m->nrec) {
+        // the trace layout changed: a caller buffer no longer fits, an owned one is re-laid out
+        if (!m->traces_owned)
+            m->traces = nullptr;
+        m->trace_rows = 0;
+    }
+    m->nrec = nrec;
+    m->rec_dense.swap(dense);
+    m->pending_row = -1;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_set_trace_buffer(fd_model *m, float *traces_dev, int nt_rows)
+{
+    NEED_MODEL(m);
+    if (nt_rows < 0)
+        return fail(FD_EINVAL, "nt_rows must be >= 0");
+    const size_t need = (size_t)nt_rows * m->nrec;
+    m->pending_row = -1;
+    m->trace_rows = 0;
+    if (traces_dev || need == 0) {
+        if (m->traces_owned) {
+            cudaStreamSynchronize(m->stream);
+            cudaFree(m->traces);
+            m->traces_owned = false;
+            m->trace_cap = 0;
+        }
+        m->traces = traces_dev;
+    } else if (!m->traces_owned || m->trace_cap < need) {
+        if (m->traces_owned) {
+            cudaStreamSynchronize(m->stream);
+            cudaFree(m->traces);
+        }
+        m->traces = nullptr;
+        m->traces_owned = false;
+        m->trace_cap = 0;
+        FD_CUDA(cudaMalloc((void **)&m->traces, need * sizeof(float)), "trace allocation");
+        m->traces_owned = true;
+        m->trace_cap = need;
+    }
+    if (need > 0 && m->traces)
+        FD_CUDA(cudaMemsetAsync(m->traces, 0, need * sizeof(float), m->stream), "trace clear");
+    m->trace_rows = nt_rows;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_reset(fd_model *m)
+{
+    NEED_MODEL(m);
+    const size_t bytes = m->pitched * sizeof(float);
+    FD_CUDA(cudaMemsetAsync(m->buf[0], 0, bytes, m->stream), "reset");
+    FD_CUDA(cudaMemsetAsync(m->buf[1], 0, bytes, m->stream), "reset");
+    m->n = 0;
+    m->pending_row = -1;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_set_wavefield(fd_model *m, const float *p_host, const float *pold_host, int n)
+{
+    NEED_MODEL(m);
+    if (!p_host || !pold_host || n < 0)
+        return fail(FD_EINVAL, "bad wavefield arguments");
+    const size_t wb = (size_t)m->nx * 4, pb = (size_t)m->px * 4;
+    FD_CUDA(cudaMemcpy2DAsync(m->buf[m->cur], pb, p_host, wb, wb, m->rows, cudaMemcpyHostToDevice, m->stream),
+            "wavefield upload");
+    FD_CUDA(cudaMemcpy2DAsync(m->buf[m->cur ^ 1], pb, pold_host, wb, wb, m->rows, cudaMemcpyHostToDevice,
+                              m->stream),
+            "wavefield upload");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "wavefield upload");
+    m->n = n;
+    m->pending_row = -1;
+    return FD_OK;
+}
+
+static fd_status flush_pending(fd_model *m)
+{
+    if (m->pending_row < 0)
+        return FD_OK;
+    cudaError_t e = launch_gather(m->buf[m->cur], m->d_rec, m->nrec, m->traces + (size_t)m->pending_row * m->nrec,
+                                  m->stream);
+    ++g_launches;
+    m->pending_row = -1;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "receiver gather");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_step(fd_model *m, int nsteps)
+{
+    NEED_MODEL(m);
+    if (nsteps < 0)
+        return fail(FD_EINVAL, "nsteps must be >= 0");
+    StepParams p{};
+    float w4[4];
+    fd_stencil_weights(w4);
+    p.c1 = w4[0];
+    p.c2 = w4[1];
+    p.c3 = w4[2];
+    p.c4 = w4[3];
+    p.ax = m->ax;
+    p.ay = m->ay;
+    p.az = m->az;
+    p.nx = m->nx;
+    p.ny = m->ny;
+    p.nz = m->nz;
+    p.px = m->px;
+    p.bz = m->bz;
+    p.has_sponge = m->has_sponge;
+    p.sx = m->sx;
+    p.sy = m->sy;
+    p.sz = m->sz;
+    p.rec_idx = m->d_rec;
+    p.nrec = m->nrec;
+    p.err = m->d_err;
+    for (int s = 0; s < nsteps; ++s) {
+        const int c = m->cur;
+        p.out = m->buf[c ^ 1];
+        p.P = m->buf[c];
+        p.src_on = m->src_on && m->n < (int)m->amp.size();
+        p.src_amp = p.src_on ? m->amp[m->n] : 0.f;
+        p.trace_prev = m->pending_row >= 0 ? m->traces + (size_t)m->pending_row * m->nrec : nullptr;
+        cudaError_t e = m->d.ndim == 3
+                            ? launch_step3d(m->halo_map[c], m->tile_map[c ^ 1], m->w_map, p, m->nchunks, m->stream)
+                            : launch_step2d(m->halo_map[c], m->tile_map[c ^ 1], m->w_map, p, m->stream);
+        ++g_launches;
+        if (e != cudaSuccess)
+            return cuda_fail(e, "step kernel launch");
+        m->cur ^= 1;
+        m->pending_row = (m->nrec > 0 && m->traces && m->n < m->trace_rows) ? m->n : -1;
+        ++m->n;
+    }
+    return flush_pending(m);
+}
+
+extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
+{
+    NEED_MODEL(m);
+    if (nt < 0)
+        return fail(FD_EINVAL, "nt must be >= 0");
+    fd_status st = fd_reset(m);
+    if (st)
+        return st;
+    st = fd_set_trace_buffer(m, traces_dev, nt);
+    if (st)
+        return st;
+    return fd_step(m, nt);
+}
+
+extern "C" fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap)
+{
+    NEED_MODEL(m);
+    const size_t need = (size_t)m->trace_rows * m->nrec;
+    if (need > 0 && (!host_out || cap < need))
+        return fail(FD_EINVAL, "trace output needs %zu floats (got %zu)", need, cap);
+    if (need > 0 && m->traces)
+        FD_CUDA(cudaMemcpyAsync(host_out, m->traces, need * sizeof(float), cudaMemcpyDeviceToHost, m->stream),
+                "trace download");
+    return fd_synchronize(m);
+}
+
+extern "C" fd_status fd_get_wavefield(fd_model *m, float *p_host, float *pold_host, size_t cap)
+{
+    NEED_MODEL(m);
+    if (!p_host || cap < m->npts)
+        return fail(FD_EINVAL, "wavefield output needs %zu floats (got %zu)", m->npts, cap);
+    const size_t wb = (size_t)m->nx * 4, pb = (size_t)m->px * 4;
+    FD_CUDA(cudaMemcpy2DAsync(p_host, wb, m->buf[m->cur], pb, wb, m->rows, cudaMemcpyDeviceToHost, m->stream),
+            "wavefield download");
+    if (pold_host)
+        FD_CUDA(cudaMemcpy2DAsync(pold_host, wb, m->buf[m->cur ^ 1], pb, wb, m->rows, cudaMemcpyDeviceToHost,
+                                  m->stream),
+                "wavefield download");
+    return fd_synchronize(m);
+}
+
+extern "C" fd_status fd_synchronize(fd_model *m)
+{
+    NEED_MODEL(m);
+    FD_CUDA(cudaStreamSynchronize(m->stream), "stream synchronize");
+    int err = 0;
+    FD_CUDA(cudaMemcpy(&err, m->d_err, sizeof err, cudaMemcpyDeviceToHost), "error word");
+    if (err) {
+        cudaMemset(m->d_err, 0, sizeof(int));
+        return fail(FD_ETIMEOUT, "a kernel gave up a bounded wait (device code %d)", err);
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_get_step(fd_model *m, int *n)
+{
+    if (!m || !n)
+        return fail(FD_EINVAL, "NULL argument");
+    *n = m->n;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_get_source_index(fd_model *m, int64_t *idx)
+{
+    if (!m || !idx)
+        return fail(FD_EINVAL, "NULL argument");
+    *idx = m->src_on ? ((int64_t)m->sz * m->ny + m->sy) * m->nx + m->sx : -1;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_get_receiver_indices(fd_model *m, int64_t *out, int cap)
+{
+    if (!m || (m->nrec > 0 && !out))
+        return fail(FD_EINVAL, "NULL argument");
+    if (cap < m->nrec)
+        return fail(FD_EINVAL, "need room for %d indices", m->nrec);
+    std::copy(m->rec_dense.begin(), m->rec_dense.end(), out);
+    return FD_OK;
+}
+
+extern "C" fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap)
+{
+    NEED_MODEL(m);
+    if (axis < 0 || axis > 2 || !out)
+        return fail(FD_EINVAL, "bad axis or NULL output");
+    const int n = axis == 0 ? m->nx : axis == 1 ? m->ny : m->nz;
+    if (cap < n)
+        return fail(FD_EINVAL, "need room for %d floats", n);
+    const float *src = axis == 0 ? m->ax : axis == 1 ? m->ay : m->az;
+    FD_CUDA(cudaMemcpyAsync(out, src, (size_t)n * 4, cudaMemcpyDeviceToHost, m->stream), "profile download");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "profile download");
+    return FD_OK;
+}
+
+extern "C" uint64_t fd_kernel_launch_count(void)
+{
+    return g_launches.load();
+}
+
+extern "C" const char *fd_last_error(void)
+{
+    return g_last_error.c_str();
+}

@@ -1,0 +1,65 @@
+// fd_internal.h -- parameters and launchers shared by the host API and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace fdk {
+
+constexpr int kRadius = 4;
+
+// 3D step: a CTA owns a kTX3 x kTY3 column of the (x, y) plane and marches
+// along z through bz planes; kStages3 haloed planes are in flight in shared
+// memory at once.
+constexpr int kTX3 = 64;
+constexpr int kTY3 = 16;
+constexpr int kStages3 = 7;
+constexpr int kThreads3 = kTX3 / 4 * kTY3 + 32;   // consumers + one producer warp
+
+// 2D step: a CTA owns one kTX2 x kTZ2 tile.
+constexpr int kTX2 = 64;
+constexpr int kTZ2 = 16;
+constexpr int kThreads2 = kTX2 / 4 * kTZ2;
+
+// Codes a kernel writes into the model's device error word.
+constexpr int kDevErrTimeout = 1;
+
+// Everything one time step needs besides the three tensor maps.
+struct StepParams {
+    float *out;               // Pn destination: the Pold buffer, pitched
+    const float *P;           // level n, pitched (read by the receiver gather)
+    const float *ax;          // damping a = dt * eta along x (px entries, 0 past nx)
+    const float *ay;          // ... along y (ny entries)
+    const float *az;          // ... along z (nz entries)
+    float c1, c2, c3, c4;     // stencil weights
+    int nx, ny, nz, px;       // extents and x pitch (elements)
+    int bz;                   // z planes per CTA (3D)
+    int has_sponge;
+    int src_on, sx, sy, sz;   // source point, active this step if src_on
+    float src_amp;            // dt^2 S(t_n) / h^d
+    const int64_t *rec_idx;   // receivers' pitched linear indices
+    int nrec;
+    float *trace_prev;        // if set: trace_prev[r] = P[rec_idx[r]] (previous step's row)
+    int *err;                 // device error word
+};
+
+size_t step3d_smem_bytes();
+cudaError_t step3d_prepare();
+int step3d_blocks_per_sm();
+cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
+                          const StepParams &p, int nchunks, cudaStream_t s);
+cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
+                          const StepParams &p, cudaStream_t s);
+cudaError_t launch_gather(const float *P, const int64_t *idx, int nrec, float *out, cudaStream_t s);
+// Over the nx valid columns of a pitched [rows][px] velocity: stats[0] |= bit
+// pattern of the largest finite positive value, stats[1] += count of entries
+// that are not finite and positive.  stats must start at zero.
+cudaError_t launch_velocity_stats(const float *v, int nx, size_t rows, int px, unsigned *stats,
+                                  cudaStream_t s);
+// w = (dt/h * v)^2 rounded to FP32 over the pitched layout (v may alias w).
+cudaError_t launch_compute_w(const float *v, float *w, int nx, size_t rows, int px, double dt_over_h,
+                             cudaStream_t s);
+
+}  // namespace fdk

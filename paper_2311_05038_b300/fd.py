@@ -1,0 +1,330 @@
+"""Python binding of libfd (include/fd.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: all propagation work runs in the CUDA kernels of
+libfd.so.  Importing this module fails loudly if the library has not been
+built; there is no CPU fallback.
+
+Host arrays are numpy arrays (copied by the library); device arrays are torch
+CUDA tensors, passed by pointer to the ``*_dev`` entry points (never owned).
+Streams are ``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libfd.so is not built ({LIB_PATH}); run `python -m paper_2311_05038_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FD_OK, FD_EINVAL, FD_ECFL, FD_ERANGE, FD_ENOMEM, FD_EBUDGET, FD_ECUDA, FD_ETIMEOUT, FD_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+STATUS_NAMES = {0: "FD_OK", -1: "FD_EINVAL", -2: "FD_ECFL", -3: "FD_ERANGE", -4: "FD_ENOMEM",
+                -5: "FD_EBUDGET", -6: "FD_ECUDA", -7: "FD_ETIMEOUT", -8: "FD_ESTATE"}
+
+# Every entry point declared in include/fd.h.
+EXPORTS = [
+    "fd_cfl_limit", "fd_stencil_weights", "fd_model_create", "fd_model_create_dev", "fd_model_destroy",
+    "fd_set_velocity", "fd_set_velocity_dev", "fd_set_source", "fd_set_receivers", "fd_set_trace_buffer",
+    "fd_reset", "fd_set_wavefield", "fd_step", "fd_run_shot", "fd_gather_traces", "fd_get_wavefield",
+    "fd_synchronize", "fd_get_step", "fd_get_source_index", "fd_get_receiver_indices",
+    "fd_get_damping_profile", "fd_kernel_launch_count", "fd_last_error",
+]
+
+
+class FDError(RuntimeError):
+    """A libfd call returned a negative fd_status."""
+
+    def __init__(self, status: int, func: str, msg: str):
+        self.status = status
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class fd_grid_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double), ("sponge_width", ctypes.c_int),
+                ("sponge_R", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_sz = ctypes.c_size_t
+
+_SIGS = {
+    "fd_cfl_limit": (ctypes.c_double, [_i]),
+    "fd_stencil_weights": (_i, [_fp]),
+    "fd_model_create": (_i, [ctypes.POINTER(fd_grid_desc), _vp, _vp, ctypes.POINTER(_vp)]),
+    "fd_model_create_dev": (_i, [ctypes.POINTER(fd_grid_desc), _vp, _vp, ctypes.POINTER(_vp)]),
+    "fd_model_destroy": (_i, [_vp]),
+    "fd_set_velocity": (_i, [_vp, _vp]),
+    "fd_set_velocity_dev": (_i, [_vp, _vp]),
+    "fd_set_source": (_i, [_vp, _i, _i, _i, _vp, _i]),
+    "fd_set_receivers": (_i, [_vp, _vp, _i]),
+    "fd_set_trace_buffer": (_i, [_vp, _vp, _i]),
+    "fd_reset": (_i, [_vp]),
+    "fd_set_wavefield": (_i, [_vp, _vp, _vp, _i]),
+    "fd_step": (_i, [_vp, _i]),
+    "fd_run_shot": (_i, [_vp, _i, _vp]),
+    "fd_gather_traces": (_i, [_vp, _vp, _sz]),
+    "fd_get_wavefield": (_i, [_vp, _vp, _vp, _sz]),
+    "fd_synchronize": (_i, [_vp]),
+    "fd_get_step": (_i, [_vp, _ip]),
+    "fd_get_source_index": (_i, [_vp, _i64p]),
+    "fd_get_receiver_indices": (_i, [_vp, _vp, _i]),
+    "fd_get_damping_profile": (_i, [_vp, _i, _vp, _i]),
+    "fd_kernel_launch_count": (ctypes.c_uint64, []),
+    "fd_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _check(status: int, func: str):
+    if status != FD_OK:
+        raise FDError(status, func, _lib.fd_last_error().decode())
+
+
+def _host_f32(a, n=None):
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t) -> int:
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("device arrays must be contiguous torch CUDA tensors")
+    return int(t.data_ptr())
+
+
+# ------------------------------------------------------------------ entry points
+
+def fd_cfl_limit(ndim: int) -> float:
+    return float(_lib.fd_cfl_limit(int(ndim)))
+
+
+def fd_stencil_weights() -> np.ndarray:
+    out = np.zeros(4, np.float32)
+    _check(_lib.fd_stencil_weights(out.ctypes.data_as(_fp)), "fd_stencil_weights")
+    return out
+
+
+def make_desc(ndim, nx, ny, nz, h, dt, sponge_width=0, sponge_R=1e-3) -> fd_grid_desc:
+    return fd_grid_desc(int(ndim), int(nx), int(ny), int(nz), float(h), float(dt), int(sponge_width),
+                        float(sponge_R))
+
+
+def fd_model_create(desc: fd_grid_desc, v_host, stream=None) -> int:
+    v = _host_f32(v_host, desc.nx * desc.ny * desc.nz)
+    out = _vp()
+    _check(_lib.fd_model_create(ctypes.byref(desc), v.ctypes.data, _stream_ptr(stream), ctypes.byref(out)),
+           "fd_model_create")
+    return out.value
+
+
+def fd_model_create_dev(desc: fd_grid_desc, v_dev, stream=None) -> int:
+    if v_dev.numel() != desc.nx * desc.ny * desc.nz:
+        raise ValueError("velocity size does not match the grid")
+    out = _vp()
+    _check(_lib.fd_model_create_dev(ctypes.byref(desc), _dev_ptr(v_dev), _stream_ptr(stream),
+                                    ctypes.byref(out)), "fd_model_create_dev")
+    return out.value
+
+
+def fd_model_destroy(m: int):
+    _check(_lib.fd_model_destroy(m), "fd_model_destroy")
+
+
+def fd_set_velocity(m: int, v_host, n=None):
+    v = _host_f32(v_host, n)
+    _check(_lib.fd_set_velocity(m, v.ctypes.data), "fd_set_velocity")
+
+
+def fd_set_velocity_ptr(m: int, host_ptr: int):
+    """fd_set_velocity from a raw host pointer (e.g. a pinned torch tensor)."""
+    _check(_lib.fd_set_velocity(m, host_ptr), "fd_set_velocity")
+
+
+def fd_set_velocity_dev(m: int, v_dev):
+    _check(_lib.fd_set_velocity_dev(m, _dev_ptr(v_dev)), "fd_set_velocity_dev")
+
+
+def fd_set_source(m: int, ix: int, iy: int, iz: int, wavelet=None):
+    if wavelet is None:
+        _check(_lib.fd_set_source(m, int(ix), int(iy), int(iz), None, 0), "fd_set_source")
+        return
+    w = _host_f32(wavelet)
+    _check(_lib.fd_set_source(m, int(ix), int(iy), int(iz), w.ctypes.data, int(w.size)), "fd_set_source")
+
+
+def fd_set_receivers(m: int, xyz):
+    r = np.ascontiguousarray(np.asarray(xyz, dtype=np.int32).reshape(-1, 3))
+    _check(_lib.fd_set_receivers(m, r.ctypes.data if len(r) else None, int(len(r))), "fd_set_receivers")
+
+
+def fd_set_trace_buffer(m: int, traces_dev, nt_rows: int):
+    ptr = None if traces_dev is None else _dev_ptr(traces_dev)
+    _check(_lib.fd_set_trace_buffer(m, ptr, int(nt_rows)), "fd_set_trace_buffer")
+
+
+def fd_reset(m: int):
+    _check(_lib.fd_reset(m), "fd_reset")
+
+
+def fd_set_wavefield(m: int, p_host, pold_host, n: int = 0):
+    p = _host_f32(p_host)
+    po = _host_f32(pold_host, p.size)
+    _check(_lib.fd_set_wavefield(m, p.ctypes.data, po.ctypes.data, int(n)), "fd_set_wavefield")
+
+
+def fd_step(m: int, nsteps: int):
+    _check(_lib.fd_step(m, int(nsteps)), "fd_step")
+
+
+def fd_run_shot(m: int, nt: int, traces_dev=None):
+    ptr = None if traces_dev is None else _dev_ptr(traces_dev)
+    _check(_lib.fd_run_shot(m, int(nt), ptr), "fd_run_shot")
+
+
+def fd_gather_traces(m: int, out: np.ndarray):
+    """Fill the float32 host array ``out`` ([rows, nrec]) with the recorded traces."""
+    if out.dtype != np.float32 or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous float32 array")
+    _check(_lib.fd_gather_traces(m, out.ctypes.data, out.size), "fd_gather_traces")
+    return out
+
+
+def fd_gather_traces_ptr(m: int, host_ptr: int, cap: int):
+    """fd_gather_traces into a raw host pointer (e.g. a pinned torch tensor)."""
+    _check(_lib.fd_gather_traces(m, host_ptr, int(cap)), "fd_gather_traces")
+
+
+def fd_get_wavefield(m: int, shape, with_old: bool = False):
+    n = int(np.prod(shape))
+    p = np.empty(shape, np.float32)
+    po = np.empty(shape, np.float32) if with_old else None
+    _check(_lib.fd_get_wavefield(m, p.ctypes.data, None if po is None else po.ctypes.data, n),
+           "fd_get_wavefield")
+    return (p, po) if with_old else p
+
+
+def fd_synchronize(m: int):
+    _check(_lib.fd_synchronize(m), "fd_synchronize")
+
+
+def fd_get_step(m: int) -> int:
+    n = ctypes.c_int()
+    _check(_lib.fd_get_step(m, ctypes.byref(n)), "fd_get_step")
+    return n.value
+
+
+def fd_get_source_index(m: int) -> int:
+    i = ctypes.c_int64()
+    _check(_lib.fd_get_source_index(m, ctypes.byref(i)), "fd_get_source_index")
+    return i.value
+
+
+def fd_get_receiver_indices(m: int, nrec: int) -> np.ndarray:
+    out = np.zeros(max(nrec, 1), np.int64)
+    _check(_lib.fd_get_receiver_indices(m, out.ctypes.data, int(nrec)), "fd_get_receiver_indices")
+    return out[:nrec]
+
+
+def fd_get_damping_profile(m: int, axis: int, n: int) -> np.ndarray:
+    out = np.zeros(n, np.float32)
+    _check(_lib.fd_get_damping_profile(m, int(axis), out.ctypes.data, int(n)), "fd_get_damping_profile")
+    return out
+
+
+def fd_kernel_launch_count() -> int:
+    return int(_lib.fd_kernel_launch_count())
+
+
+def fd_last_error() -> str:
+    return _lib.fd_last_error().decode()
+
+
+# ------------------------------------------------------------------ convenience
+
+class Model:
+    """Owning handle of one fd_model (destroyed on close / garbage collection)."""
+
+    def __init__(self, ndim, shape, h, dt, vel, sponge_width=0, sponge_R=1e-3, stream=None):
+        if ndim == 2:
+            nz, nx = shape
+            ny = 1
+        else:
+            nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.desc = make_desc(ndim, nx, ny, nz, h, dt, sponge_width, sponge_R)
+        self.nrec = 0
+        self.handle = None
+        if hasattr(vel, "is_cuda"):
+            self.handle = fd_model_create_dev(self.desc, vel, stream)
+        else:
+            self.handle = fd_model_create(self.desc, vel, stream)
+
+    @classmethod
+    def from_shot(cls, shot, stream=None):
+        m = cls(shot.ndim, shot.shape, shot.h, shot.dt, shot.vel, shot.sponge_width, shot.sponge_R, stream)
+        m.set_source(shot.src, shot.wavelet)
+        m.set_receivers(shot.receivers)
+        return m
+
+    def set_source(self, xyz, wavelet):
+        fd_set_source(self.handle, xyz[0], xyz[1], xyz[2], wavelet)
+
+    def set_receivers(self, xyz):
+        r = np.asarray(xyz, dtype=np.int32).reshape(-1, 3)
+        fd_set_receivers(self.handle, r)
+        self.nrec = len(r)
+
+    def run_shot(self, nt, traces_dev=None):
+        fd_run_shot(self.handle, nt, traces_dev)
+
+    def step(self, n):
+        fd_step(self.handle, n)
+
+    def traces(self, rows):
+        out = np.empty((rows, self.nrec), np.float32)
+        return fd_gather_traces(self.handle, out)
+
+    def wavefield(self, with_old=False):
+        return fd_get_wavefield(self.handle, self.shape, with_old)
+
+    def close(self):
+        if self.handle:
+            fd_model_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

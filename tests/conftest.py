@@ -18,3 +18,20 @@ def oracle():
     from oracle import oracle as o
     o.build()
     return o
+
+
+@pytest.fixture(scope="session")
+def fdlib():
+    """The CUDA library's binding, built in place first if its sources changed."""
+    from paper_2311_05038_b300.build import build
+    build()
+    import paper_2311_05038_b300.fd as fd
+    return fd
+
+
+def cuda_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

@@ -1,0 +1,254 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a CUDA device).
+
+The procedure is the paper's generic test (section 6): inputs are built on the
+host, copied in, the routine runs, outputs are copied back and compared on the
+host.  Floating-point results must match the oracle within a relative L2
+error of 1e-4 (wavefield and traces); integer maps (source and receiver
+indices, sponge band extents) must match exactly.
+"""
+import numpy as np
+import pytest
+
+import pinlib as pl
+import workloads as wl
+from conftest import cuda_available
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+TOL = 1e-4
+
+
+def gpu_run(fd, shot, nt, P0=None, Pold0=None):
+    with fd.Model.from_shot(shot) as m:
+        if P0 is None:
+            m.run_shot(nt)
+        else:
+            fd.fd_set_trace_buffer(m.handle, None, nt)
+            fd.fd_set_wavefield(m.handle, P0, Pold0, 0)
+            m.step(nt)
+        tr = m.traces(nt)
+        P, Pold = m.wavefield(with_old=True)
+    return P, Pold, tr
+
+
+def oracle_run(oracle, shot, nt, P0=None, Pold0=None):
+    return oracle.run(shot.ndim, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width,
+                      sponge_R=shot.sponge_R, src=shot.src, wavelet=shot.wavelet, receivers=shot.receivers,
+                      P=P0, Pold=Pold0, nsteps=nt)
+
+
+def assert_parity(gpu, ref, what):
+    P, Pold, tr = gpu
+    Pr, Poldr, trr = ref
+    assert np.all(np.isfinite(P)) and np.all(np.isfinite(tr))
+    e_p = pl.rel_l2(P, Pr)
+    e_o = pl.rel_l2(Pold, Poldr)
+    e_t = pl.rel_l2(tr, trr)
+    assert e_p <= TOL and e_o <= TOL and e_t <= TOL, (what, e_p, e_o, e_t)
+    return e_p, e_t
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_parity_2d_workload(fdlib, oracle):
+    """256 x 256, 500 steps, 15 Hz Ricker, 64 receivers, rigid boundaries."""
+    shot = wl.parity_2d()
+    assert_parity(gpu_run(fdlib, shot, shot.nt), oracle_run(oracle, shot, shot.nt), "2d")
+
+
+def test_parity_2d_ragged_sponge(fdlib, oracle):
+    """Ragged 53 x 77 grid (tiles 64 x 16 leave tails), random velocity, sponge 6."""
+    shape = (53, 77)
+    vel = wl.grf_velocity(shape, corr_cells=6.0, seed=21)
+    dt = wl.courant_dt(10.0, float(vel.max()))
+    nt = 400
+    rng = np.random.default_rng(22)
+    rec = np.array([(ix, 0, 11) for ix in range(0, 77, 3)] +
+                   [(int(rng.integers(0, 77)), 0, int(rng.integers(0, 53))) for _ in range(20)], np.int32)
+    shot = wl.Shot(2, shape, 10.0, dt, nt, vel, (30, 0, 20), wl.ricker(nt, dt, 20.0), rec, sponge_width=6)
+    assert_parity(gpu_run(fdlib, shot, nt), oracle_run(oracle, shot, nt), "2d ragged")
+
+
+def test_parity_3d_ragged_sponge(fdlib, oracle):
+    """45 x 38 x 70 grid: several (x, y) tiles with tails, two z chunks, sponge 8."""
+    shot = wl.roofline_3d(shape=(45, 38, 70), nt=300, sponge_width=8)
+    assert_parity(gpu_run(fdlib, shot, shot.nt), oracle_run(oracle, shot, shot.nt), "3d ragged")
+
+
+def test_parity_3d_layered_96(fdlib, oracle):
+    """The layered 3D workload at 96^3 with a 20-point sponge, 400 steps."""
+    shot = wl.roofline_3d(n=96, nt=400, sponge_width=20)
+    assert_parity(gpu_run(fdlib, shot, shot.nt), oracle_run(oracle, shot, shot.nt), "3d 96")
+
+
+def test_parity_3d_full_size_from_random_state(fdlib, oracle):
+    """512^3 layered workload (the benchmark's launch configuration), random initial
+    levels so every point, face and sponge band is active, 3 steps with the source on."""
+    shot = wl.roofline_3d(n=512, nt=3)
+    P0, Pm1 = wl.random_state(shot.shape, seed=31)
+    gpu = gpu_run(fdlib, shot, 3, P0, Pm1)
+    ref = oracle_run(oracle, shot, 3, P0, Pm1)
+    assert_parity(gpu, ref, "3d 512 state")
+    # pointwise: FP32 rounding of a few steps only
+    err = np.max(np.abs(gpu[0] - ref[0])) / np.max(np.abs(ref[0]))
+    assert err < 1e-5, err
+
+
+def test_full_size_reciprocity(fdlib):
+    """512^3, 1000 steps, sponge on: v_s^2 P_(s->r) = v_r^2 P_(r->s) on the GPU."""
+    shot = wl.roofline_3d(n=512, nt=1000)
+    s = shot.src
+    r = (shot.nx // 2 + 60, shot.ny // 2 - 40, 25 + 60)
+    v = shot.vel
+    vs, vr = float(v[s[2], s[1], s[0]]), float(v[r[2], r[1], r[0]])
+    out = []
+    for a, b in ((s, r), (r, s)):
+        sh = wl.Shot(3, shot.shape, shot.h, shot.dt, shot.nt, v, a, shot.wavelet,
+                     np.array([b], np.int32), sponge_width=shot.sponge_width)
+        with fdlib.Model.from_shot(sh) as m:
+            m.run_shot(shot.nt)
+            out.append(m.traces(shot.nt)[:, 0].astype(np.float64))
+    lhs, rhs = vs * vs * out[0], vr * vr * out[1]
+    assert np.max(np.abs(lhs)) > 0
+    assert pl.rel_l2(lhs, rhs) < TOL
+
+
+# ------------------------------------------------------------------ exact maps
+
+def test_index_maps_are_exact(fdlib, oracle):
+    shot = wl.roofline_3d(shape=(40, 36, 50), nt=4, sponge_width=7)
+    with fdlib.Model.from_shot(shot) as m:
+        nz, ny, nx = shot.shape
+        sx, sy, sz = shot.src
+        assert fdlib.fd_get_source_index(m.handle) == (sz * ny + sy) * nx + sx
+        rec = shot.receivers.astype(np.int64)
+        want = (rec[:, 2] * ny + rec[:, 1]) * nx + rec[:, 0]
+        np.testing.assert_array_equal(fdlib.fd_get_receiver_indices(m.handle, len(rec)), want)
+        emax = oracle.sponge_eta_max(float(shot.vel.max()), 7, shot.h, shot.sponge_R)
+        for axis, n in ((0, nx), (1, ny), (2, nz)):
+            got = fdlib.fd_get_damping_profile(m.handle, axis, n)
+            ref = shot.dt * oracle.sponge_profile(n, 7, emax)
+            np.testing.assert_array_equal(got != 0, ref != 0)          # band extents, exactly
+            np.testing.assert_allclose(got, ref, rtol=2e-7, atol=0)    # values, FP32 rounding
+
+
+def test_2d_has_no_y_damping(fdlib):
+    shot = wl.parity_2d(nt=2)
+    shot.sponge_width = 5
+    with fdlib.Model.from_shot(shot) as m:
+        assert np.all(fdlib.fd_get_damping_profile(m.handle, 1, 1) == 0)
+        assert np.count_nonzero(fdlib.fd_get_damping_profile(m.handle, 0, 256)) == 10
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_steps_and_empty_receivers(fdlib):
+    shot = wl.parity_2d(nt=5)
+    with fdlib.Model.from_shot(shot) as m:
+        m.run_shot(0)
+        assert m.traces(0).shape == (0, 64)
+        assert np.all(m.wavefield() == 0)
+        m.set_receivers(np.zeros((0, 3), np.int32))
+        m.run_shot(5)
+        assert m.traces(5).shape == (5, 0)
+        assert np.any(m.wavefield() != 0)
+
+
+def test_split_steps_equal_one_call_bitwise(fdlib):
+    shot = wl.roofline_3d(shape=(33, 20, 40), nt=12, sponge_width=4)
+    with fdlib.Model.from_shot(shot) as m:
+        m.run_shot(12)
+        P1, tr1 = m.wavefield(), m.traces(12)
+        fdlib.fd_reset(m.handle)
+        fdlib.fd_set_trace_buffer(m.handle, None, 12)
+        for n in (3, 0, 5, 4):
+            m.step(n)
+        assert fdlib.fd_get_step(m.handle) == 12
+        np.testing.assert_array_equal(m.wavefield(), P1)
+        np.testing.assert_array_equal(m.traces(12), tr1)
+
+
+def test_deterministic_bitwise(fdlib):
+    shot = wl.roofline_3d(n=64, nt=30)
+    a = gpu_run(fdlib, shot, 30)
+    b = gpu_run(fdlib, shot, 30)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (1, 9), (9, 1), (2, 3, 1), (1, 1, 1), (5, 3, 4)])
+def test_tiny_grids(fdlib, oracle, shape):
+    ndim = len(shape)
+    rng = np.random.default_rng(41)
+    vel = rng.uniform(1500, 2500, shape).astype(np.float32)
+    dt = 0.3 * 10.0 / float(vel.max())
+    nt = 25
+    pts = [(0, 0, 0), (shape[-1] - 1, 0 if ndim == 2 else shape[1] - 1, shape[0] - 1)]
+    rec = np.array(pts, np.int32)
+    shot = wl.Shot(ndim, shape, 10.0, dt, nt, vel, pts[-1], wl.ricker(nt, dt, 30.0), rec)
+    P0, Pm1 = wl.random_state(shape, seed=42)
+    assert_parity(gpu_run(fdlib, shot, nt, P0, Pm1), oracle_run(oracle, shot, nt, P0, Pm1), f"tiny {shape}")
+
+
+def test_source_and_receivers_at_corners(fdlib, oracle):
+    shape = (30, 18, 26)
+    vel = wl.layered_velocity(shape, seed=5)
+    dt = wl.courant_dt(10.0, float(vel.max()))
+    nt = 60
+    nz, ny, nx = shape
+    corners = [(x, y, z) for z in (0, nz - 1) for y in (0, ny - 1) for x in (0, nx - 1)]
+    shot = wl.Shot(3, shape, 10.0, dt, nt, vel, (0, 0, 0), wl.ricker(nt, dt, 40.0),
+                   np.array(corners, np.int32), sponge_width=5)
+    assert_parity(gpu_run(fdlib, shot, nt), oracle_run(oracle, shot, nt), "corners")
+
+
+# ------------------------------------------------------------------ errors
+
+def test_out_of_range_points_are_erange(fdlib):
+    shot = wl.roofline_3d(shape=(20, 20, 20), nt=5, sponge_width=0)
+    with fdlib.Model.from_shot(shot) as m:
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_set_source(m.handle, 20, 0, 0, shot.wavelet)
+        assert e.value.status == fdlib.FD_ERANGE
+        with pytest.raises(fdlib.FDError) as e:
+            m.set_receivers(np.array([(0, 0, 0), (0, -1, 3)], np.int32))
+        assert e.value.status == fdlib.FD_ERANGE
+        # the rejected calls changed nothing
+        assert fdlib.fd_get_source_index(m.handle) == (shot.src[2] * 20 + shot.src[1]) * 20 + shot.src[0]
+        np.testing.assert_array_equal(fdlib.fd_get_receiver_indices(m.handle, len(shot.receivers)),
+                                      (shot.receivers[:, 2].astype(np.int64) * 20 + shot.receivers[:, 1]) * 20
+                                      + shot.receivers[:, 0])
+
+
+def test_rejected_velocity_leaves_model_unchanged(fdlib):
+    import torch
+    shot = wl.roofline_3d(shape=(24, 20, 36), nt=20, sponge_width=4)
+    with fdlib.Model.from_shot(shot) as m:
+        m.run_shot(20)
+        P1 = m.wavefield()
+        fast = np.full(shot.vel.size, 1e5, np.float32)
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_set_velocity(m.handle, fast)
+        assert e.value.status == fdlib.FD_ECFL
+        bad = torch.full((shot.vel.size,), 2000.0, device="cuda")
+        bad[17] = float("nan")
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_set_velocity_dev(m.handle, bad)
+        assert e.value.status == fdlib.FD_EINVAL
+        m.run_shot(20)
+        np.testing.assert_array_equal(m.wavefield(), P1)
+
+
+def test_device_inputs_match_host_inputs(fdlib):
+    import torch
+    shot = wl.roofline_3d(shape=(24, 20, 36), nt=15, sponge_width=4)
+    a = gpu_run(fdlib, shot, 15)
+    v_dev = torch.from_numpy(shot.vel.ravel()).cuda()
+    traces = torch.zeros((15, len(shot.receivers)), device="cuda")
+    with fdlib.Model(3, shot.shape, shot.h, shot.dt, v_dev, shot.sponge_width) as m:
+        m.set_source(shot.src, shot.wavelet)
+        m.set_receivers(shot.receivers)
+        m.run_shot(15, traces)
+        fdlib.fd_synchronize(m.handle)
+        np.testing.assert_array_equal(m.wavefield(), a[0])
+    np.testing.assert_array_equal(traces.cpu().numpy(), a[2])
