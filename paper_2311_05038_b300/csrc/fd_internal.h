@@ -11,12 +11,29 @@ namespace fdk {
 constexpr int kRadius = 4;
 
 // 3D step: a CTA owns a kTX3 x kTY3 column of the (x, y) plane and marches
-// along z through bz planes; kStages3 haloed planes are in flight in shared
-// memory at once.
-constexpr int kTX3 = 64;
-constexpr int kTY3 = 16;
-constexpr int kStages3 = 7;
-constexpr int kThreads3 = kTX3 / 4 * kTY3 + 32;   // consumers + one producer warp
+// along z through bz planes, fed by two TMA rings in shared memory.
+// Compile-time knobs (defaults are the tuned configuration).
+#ifndef FD_TX3
+#define FD_TX3 64
+#endif
+#ifndef FD_TY3
+#define FD_TY3 16
+#endif
+#ifndef FD_STAGESP3
+#define FD_STAGESP3 11
+#endif
+#ifndef FD_STAGEST3
+#define FD_STAGEST3 4
+#endif
+#ifndef FD_MINB3
+#define FD_MINB3 2
+#endif
+constexpr int kTX3 = FD_TX3;
+constexpr int kTY3 = FD_TY3;
+constexpr int kStagesP3 = FD_STAGESP3;   // haloed P planes in flight
+constexpr int kStagesT3 = FD_STAGEST3;   // Pold + w tiles in flight
+constexpr int kMinBlocks3 = FD_MINB3;
+constexpr int kThreads3 = kTX3 / 4 * kTY3;
 
 // 2D step: a CTA owns one kTX2 x kTZ2 tile.
 constexpr int kTX2 = 64;

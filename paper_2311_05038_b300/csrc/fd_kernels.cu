@@ -27,6 +27,23 @@ __device__ __forceinline__ float f4c(const float4 &v, int e)
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
+__device__ __forceinline__ float2 half2of(const float4 &v, int h)
+{
+    return h == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+}
+
+// x pair sums P[x+k] + P[x-k] for the two points (2h, 2h+1) of a thread whose
+// row segment x-4 .. x+7 is xa[0..11].  Even k keeps both operands on aligned
+// register pairs (one packed add); odd k straddles them (two scalar adds with
+// the same rounding).
+__device__ __forceinline__ float2 xpair2(const float (&xa)[12], int h, int k)
+{
+    const int i = 4 + 2 * h;
+    if ((k & 1) == 0)
+        return __fadd2_rn(make_float2(xa[i + k], xa[i + k + 1]), make_float2(xa[i - k], xa[i - k + 1]));
+    return make_float2(xa[i + k] + xa[i - k], xa[i + k + 1] + xa[i - k + 1]);
+}
+
 // Damped leapfrog update of one point from its centre value, Pold, w, damping a
 // and the four distance sums S_k over NDIM axes.
 template <int NDIM>
@@ -61,38 +78,48 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 
 // ----------------------------------------------------------------------------- 3D
 
-// A CTA owns the column [x0, x0+TX) x [y0, y0+TY) and output planes [z0, z1).
-// Warps 0..NCW-1 are consumers (each thread: 4 consecutive x points of one row);
-// warp NCW's lane 0 is the producer issuing TMA loads.  Ring stage k holds the
-// haloed P plane z0-4+k and, for k >= 8, the Pold and w planes z0-8+k.  A
-// consumer computing plane z = z0+j reads its z neighbours from a 9-deep
-// register queue, its x/y neighbours from stage j+4 (plane z) and Pold, w from
-// stage j+8, then frees stage j+4.
-template <int TX, int TY, int S>
-__global__ void __launch_bounds__(TX / 4 * TY + 32, 2)
+// A CTA owns the column [x0, x0+TX) x [y0, y0+TY) and output planes [z0, z1);
+// each of its TX/4*TY threads computes 4 consecutive x points of one row.
+//
+// Two TMA rings feed it.  The P ring (SP slots) holds haloed P planes: stage k
+// is plane z0-4+k, k = 0 .. nb+7.  The T ring (ST slots) holds the Pold and w
+// tiles of output plane z0+t, t = 0 .. nb-1.  Computing plane z = z0+j needs P
+// stages j+4 (x/y neighbours, the plane itself) and j+8 (the newest plane; its
+// centre enters a 9-deep register queue that supplies the z neighbours) and T
+// stage j.  Afterwards the warp frees P stage j+4 and T stage j.
+//
+// There is no producer thread: a per-slot shared counter finds the last warp to
+// free a slot, and that warp issues the slot's next stage at once, so loads run
+// SP-5 P stages and ST-1 T stages ahead of the slowest warp without anyone
+// blocking.  The only waits are the bounded waits on the full barriers.
+template <int TX, int TY, int SP, int ST>
+__global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
 {
     constexpr int QX = TX / 4;
-    constexpr int NCONS = QX * TY;
-    constexpr int NCW = NCONS / 32;
+    constexpr int NT = QX * TY;
+    constexpr int NW = NT / 32;
     constexpr int HX = TX + 8;
     constexpr int HY = TY + 8;
     constexpr int PBOX = HX * HY;
     constexpr int TBOX = TX * TY;
     constexpr uint32_t BYTES_P = PBOX * 4;
     constexpr uint32_t BYTES_T = TBOX * 4;
-    static_assert(NCONS % 32 == 0, "consumer threads must fill warps");
+    static_assert(NT % 32 == 0, "threads must fill warps");
     static_assert((PBOX * 4) % 128 == 0 && (TBOX * 4) % 128 == 0, "boxes keep 128-byte alignment");
-    static_assert(S >= 5, "ring must hold planes z..z+4");
+    static_assert(SP >= 9, "P ring must hold planes z..z+4 and run ahead");
+    static_assert(ST >= 2, "T ring must run ahead");
 
     extern __shared__ __align__(128) unsigned char smem[];
     float *sP = reinterpret_cast<float *>(smem);
-    float *sO = sP + S * PBOX;
-    float *sW = sO + S * TBOX;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sW + S * TBOX);
-    uint64_t *empty = full + S;
+    float *sT = sP + SP * PBOX;                       // [ST][Pold tile, w tile]
+    uint64_t *fullP = reinterpret_cast<uint64_t *>(sT + ST * 2 * TBOX);
+    uint64_t *fullT = fullP + SP;
+    unsigned *relP = reinterpret_cast<unsigned *>(fullT + ST);
+    unsigned *relT = relP + SP;
     __shared__ int s_abort;
+    __shared__ int s_issuedP, s_issuedT;
 
     const int tiles_x = (prm.nx + TX - 1) / TX;
     const int x0 = (blockIdx.x % tiles_x) * TX;
@@ -100,98 +127,121 @@ __global__ void __launch_bounds__(TX / 4 * TY + 32, 2)
     const int z0 = blockIdx.y * prm.bz;
     const int z1 = min(prm.nz, z0 + prm.bz);
     const int nb = z1 - z0;
-    const int nstages = nb + 8;
+    const int nP = nb + 8;
     const int tid = threadIdx.x;
-    const int warp = tid >> 5;
     const int lane = tid & 31;
 
+    auto issueP = [&](int k, int slot) {
+        mbar_arrive_expect_tx(&fullP[slot], BYTES_P);
+        tma_load_3d(sP + slot * PBOX, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + k);
+        atomicAdd(&s_issuedP, 1);
+    };
+    auto issueT = [&](int t, int slot) {
+        mbar_arrive_expect_tx(&fullT[slot], 2 * BYTES_T);
+        tma_load_3d(sT + (2 * slot) * TBOX, &tmOld, &fullT[slot], x0, y0, z0 + t);
+        tma_load_3d(sT + (2 * slot + 1) * TBOX, &tmW, &fullT[slot], x0, y0, z0 + t);
+        atomicAdd(&s_issuedT, 1);
+    };
+    // Free P stage k (in slot sp) and, if t >= 0, T stage t (in slot stt); the
+    // warp completing a slot's release refills it with the stage one ring later.
+    auto release = [&](int k, int sp, int t, int stt) {
+        __syncwarp();
+        if (lane == 0) {
+            if (atomicAdd(&relP[sp], 1u) % NW == NW - 1 && k + SP < nP) {
+                fence_proxy_async_shared();
+                issueP(k + SP, sp);
+            }
+            if (t >= 0 && atomicAdd(&relT[stt], 1u) % NW == NW - 1 && t + ST < nb) {
+                fence_proxy_async_shared();
+                issueT(t + ST, stt);
+            }
+        }
+    };
+
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NCW);
+        for (int s = 0; s < SP; ++s) {
+            mbar_init(&fullP[s], 1);
+            relP[s] = 0;
+        }
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&fullT[s], 1);
+            relT[s] = 0;
         }
         s_abort = 0;
+        s_issuedP = 0;
+        s_issuedT = 0;
         fence_barrier_init();
     }
     __syncthreads();
+    if (tid == 0) {
+        prefetch_tensormap(&tmP);
+        prefetch_tensormap(&tmOld);
+        prefetch_tensormap(&tmW);
+        for (int k = 0; k < min(SP, nP); ++k)
+            issueP(k, k);
+        for (int t = 0; t < min(ST, nb); ++t)
+            issueT(t, t);
+    }
 
     gather_prev_row(prm);
 
-    if (warp == NCW) {
-        // ---------------------------------------------------------------- producer
-        if (lane == 0) {
-            prefetch_tensormap(&tmP);
-            prefetch_tensormap(&tmOld);
-            prefetch_tensormap(&tmW);
-            int issued = 0;
-            for (int k = 0; k < nstages; ++k) {
-                const int slot = k % S;
-                if (k >= S && !mbar_wait(&empty[slot], ((k / S) - 1) & 1, &s_abort)) {
-                    raise_error(prm.err, &s_abort, kDevErrTimeout);
-                    break;
-                }
-                const int pz = z0 - 4 + k;
-                const bool has_t = k >= 8;
-                mbar_arrive_expect_tx(&full[slot], BYTES_P + (has_t ? 2 * BYTES_T : 0));
-                tma_load_3d(sP + slot * PBOX, &tmP, &full[slot], x0 - 4, y0 - 4, pz);
-                if (has_t) {
-                    tma_load_3d(sO + slot * TBOX, &tmOld, &full[slot], x0, y0, pz - 4);
-                    tma_load_3d(sW + slot * TBOX, &tmW, &full[slot], x0, y0, pz - 4);
-                }
-                issued = k + 1;
-            }
-            // Do not leave while copies into this CTA's shared memory are in flight:
-            // wait (bounded, regardless of abort) for the newest use of every slot.
-            int never = 0;
-            for (int k = max(0, issued - S); k < issued; ++k)
-                mbar_wait(&full[k % S], (k / S) & 1, &never);
-        }
-        return;
-    }
-
-    // -------------------------------------------------------------------- consumers
     const int tx = tid % QX;
     const int ty = tid / QX;
     const int x = x0 + 4 * tx;
     const int y = y0 + ty;
     const int cP = (ty + 4) * HX + 4 * tx + 4;   // centre float4 within a P box
-    const int cT = ty * TX + 4 * tx;             // float4 within a Pold / w box
+    const int cT = ty * TX + 4 * tx;             // float4 within a Pold / w tile
     const bool row_ok = y < prm.ny;
 
     float axv[4] = {0.f, 0.f, 0.f, 0.f};
     float ayv = 0.f;
+    float azn = 0.f;   // az of the next output plane
     if (prm.has_sponge) {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             axv[e] = x + e < prm.px ? prm.ax[x + e] : 0.f;
         ayv = row_ok ? prm.ay[y] : 0.f;
+        azn = prm.az[z0];
     }
     const bool x_band = axv[0] != 0.f || axv[1] != 0.f || axv[2] != 0.f || axv[3] != 0.f;
+    const bool src_col = prm.src_on && y == prm.sy && (unsigned)(prm.sx - x) < 4u;
+    const bool store_vec = row_ok && x + 3 < prm.nx;
+    const bool store_any = row_ok && x < prm.nx;
+    float *const out_col = prm.out + ((size_t)z0 * prm.ny + y) * prm.px + x;
+    const size_t plane_stride = (size_t)prm.ny * prm.px;
 
-    float4 q[9];
+    // z-neighbour queue: Q[i] holds the thread's 4 points of plane z-4+i.
+    float4 Q[9];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int slot = k % S;
-        ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / S) & 1, &s_abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(&fullP[k % SP], (k / SP) & 1, &s_abort));
         if (!ok)
             break;
-        q[k] = *reinterpret_cast<const float4 *>(sP + slot * PBOX + cP);
-        if (k < 4) {
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&empty[slot]);
-        }
+        Q[k] = *reinterpret_cast<const float4 *>(sP + (k % SP) * PBOX + cP);
+        if (k < 4)
+            release(k, k % SP, -1, 0);
     }
 
-    for (int j = 0; ok && j < nb; ++j) {
-        const int k8 = j + 8;
-        const int s8 = k8 % S;
-        const int s4 = (j + 4) % S;
-        ok = __all_sync(0xffffffffu, mbar_wait(&full[s8], (k8 / S) & 1, &s_abort));
+    const float2 M2 = make_float2(-6.0f, -6.0f);
+    const float2 TWO = make_float2(2.0f, 2.0f);
+    const float2 C1 = make_float2(prm.c1, prm.c1), C2 = make_float2(prm.c2, prm.c2);
+    const float2 C3 = make_float2(prm.c3, prm.c3), C4 = make_float2(prm.c4, prm.c4);
+    // ring positions of P stage j+8 (newest), P stage j+4 (plane z) and T stage j
+    int s8 = 8 % SP, ph8 = (8 / SP) & 1;
+    int s4 = 4 % SP;
+    int st = 0, pht = 0;
+
+    auto body = [&](int j) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&fullP[s8], ph8, &s_abort) &&
+                                         mbar_wait(&fullT[st], pht, &s_abort));
         if (!ok)
-            break;
-        q[8] = *reinterpret_cast<const float4 *>(sP + s8 * PBOX + cP);
+            return;
+        const int z = z0 + j;
+        const float azv = azn;
+        if (prm.has_sponge && z + 1 < z1)
+            azn = prm.az[z + 1];
+        Q[8] = *reinterpret_cast<const float4 *>(sP + s8 * PBOX + cP);
         const float *pl = sP + s4 * PBOX + cP;
         const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
         const float4 xc = *reinterpret_cast<const float4 *>(pl);
@@ -202,56 +252,100 @@ __global__ void __launch_bounds__(TX / 4 * TY + 32, 2)
             ym[k - 1] = *reinterpret_cast<const float4 *>(pl - k * HX);
             yp[k - 1] = *reinterpret_cast<const float4 *>(pl + k * HX);
         }
-        const float4 old = *reinterpret_cast<const float4 *>(sO + s8 * TBOX + cT);
-        const float4 wv = *reinterpret_cast<const float4 *>(sW + s8 * TBOX + cT);
-        const int z = z0 + j;
-        const float ayz = prm.has_sponge ? ayv + prm.az[z] : 0.f;
-        const bool damped = x_band || ayz != 0.f;
-
+        const float4 old = *reinterpret_cast<const float4 *>(sT + (2 * st) * TBOX + cT);
+        const float4 wv = *reinterpret_cast<const float4 *>(sT + (2 * st + 1) * TBOX + cT);
         const float xa[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
-        float pn[4];
+        const float4 &pc = Q[4];
+
+        // L'P for the points (0,1) and (2,3) with packed FP32 arithmetic, in the
+        // same rounding order as update_point<3>
+        float2 acc[2];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float s[4];
+        for (int h = 0; h < 2; ++h) {
+            const float2 p2 = half2of(pc, h);
+            float2 a2;
 #pragma unroll
-            for (int k = 1; k <= 4; ++k)
-                s[k - 1] = ((xa[4 + e + k] + xa[4 + e - k]) + (f4c(yp[k - 1], e) + f4c(ym[k - 1], e))) +
-                           (f4c(q[4 + k], e) + f4c(q[4 - k], e));
-            const float a = damped ? axv[e] + ayz : 0.f;
-            pn[e] = update_point<3>(prm, f4c(q[4], e), f4c(old, e), f4c(wv, e), a, s[0], s[1], s[2], s[3]);
+            for (int k = 1; k <= 4; ++k) {
+                const float2 sx = xpair2(xa, h, k);
+                const float2 sy = __fadd2_rn(half2of(yp[k - 1], h), half2of(ym[k - 1], h));
+                const float2 sz = __fadd2_rn(half2of(Q[4 + k], h), half2of(Q[4 - k], h));
+                const float2 d = __ffma2_rn(M2, p2, __fadd2_rn(__fadd2_rn(sx, sy), sz));
+                const float2 ck = k == 1 ? C1 : k == 2 ? C2 : k == 3 ? C3 : C4;
+                a2 = k == 1 ? __fmul2_rn(ck, d) : __ffma2_rn(ck, d, a2);
+            }
+            acc[h] = a2;
         }
-        if (prm.src_on && z == prm.sz && y == prm.sy && (unsigned)(prm.sx - x) < 4u) {
+
+        float pn[4];
+        const float ayz = ayv + azv;
+        if (x_band || ayz != 0.f) {
+            // sponge band: (w L'P + 2P - (1 - a) Pold) / (1 + a), scalar
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float a = axv[e] + ayz;
+                const float lap = e == 0 ? acc[0].x : e == 1 ? acc[0].y : e == 2 ? acc[1].x : acc[1].y;
+                const float num = fmaf(f4c(wv, e), lap, fmaf(2.0f, f4c(pc, e), -(1.0f - a) * f4c(old, e)));
+                pn[e] = a != 0.0f ? num / (1.0f + a) : num;
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 o = half2of(old, h);
+                const float2 t = __ffma2_rn(TWO, half2of(pc, h), make_float2(-o.x, -o.y));
+                const float2 r = __ffma2_rn(half2of(wv, h), acc[h], t);
+                pn[2 * h] = r.x;
+                pn[2 * h + 1] = r.y;
+            }
+        }
+        if (src_col && z == prm.sz) {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 if (prm.sx - x == e)
                     pn[e] += prm.src_amp;
         }
-        if (row_ok && x < prm.nx) {
-            float *dst = prm.out + ((size_t)z * prm.ny + y) * prm.px + x;
-            if (x + 3 < prm.nx) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-            } else {
+        float *dst = out_col + (size_t)j * plane_stride;
+        if (store_vec) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        } else if (store_any) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (x + e < prm.nx)
-                        dst[e] = pn[e];
-            }
+            for (int e = 0; e < 4; ++e)
+                if (x + e < prm.nx)
+                    dst[e] = pn[e];
         }
-        __syncwarp();
-        if (lane == 0)
-            mbar_arrive(&empty[s4]);
+        release(j + 4, s4, j, st);
+        if (++s8 == SP) {
+            s8 = 0;
+            ph8 ^= 1;
+        }
+        if (++s4 == SP)
+            s4 = 0;
+        if (++st == ST) {
+            st = 0;
+            pht ^= 1;
+        }
+    };
+
+    for (int j = 0; ok && j < nb; ++j) {
+        body(j);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            q[k] = q[k + 1];
+            Q[k] = Q[k + 1];
     }
     if (ok) {
-        for (int k = nb + 4; k < nb + 8; ++k) {
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&empty[k % S]);
-        }
+        for (int k = nb + 4; k < nb + 8; ++k)
+            release(k, k % SP, -1, 0);
     } else {
         raise_error(prm.err, &s_abort, kDevErrTimeout);
+    }
+    // After an abort, do not leave while copies into this CTA's shared memory may
+    // be in flight: wait (bounded) for the newest use of every slot.
+    __syncthreads();
+    if (tid == 0 && s_abort) {
+        int never = 0;
+        for (int k = max(0, s_issuedP - SP); k < s_issuedP; ++k)
+            mbar_wait(&fullP[k % SP], (k / SP) & 1, &never, kWaitLimitCycles / 8);
+        for (int t = max(0, s_issuedT - ST); t < s_issuedT; ++t)
+            mbar_wait(&fullT[t % ST], (t / ST) & 1, &never, kWaitLimitCycles / 8);
     }
 }
 
@@ -402,26 +496,25 @@ __global__ void compute_w_kernel(const float *v, float *w, int nx, size_t rows, 
 
 // ------------------------------------------------------------------------ launchers
 
-using Step3D = decltype(&step3d_kernel<kTX3, kTY3, kStages3>);
+#define FD_STEP3D step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3>
 
 size_t step3d_smem_bytes()
 {
     constexpr int PBOX = (kTX3 + 8) * (kTY3 + 8);
     constexpr int TBOX = kTX3 * kTY3;
-    return (size_t)kStages3 * (PBOX + 2 * TBOX) * sizeof(float) + 2 * kStages3 * sizeof(uint64_t);
+    return (size_t)(kStagesP3 * PBOX + kStagesT3 * 2 * TBOX) * sizeof(float) +
+           (kStagesP3 + kStagesT3) * (sizeof(uint64_t) + sizeof(unsigned));
 }
 
 cudaError_t step3d_prepare()
 {
-    return cudaFuncSetAttribute(step3d_kernel<kTX3, kTY3, kStages3>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_smem_bytes());
+    return cudaFuncSetAttribute(FD_STEP3D, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_smem_bytes());
 }
 
 int step3d_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step3d_kernel<kTX3, kTY3, kStages3>, kThreads3,
-                                                      step3d_smem_bytes()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FD_STEP3D, kThreads3, step3d_smem_bytes()) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -431,7 +524,7 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
 {
     const int tiles = ((p.nx + kTX3 - 1) / kTX3) * ((p.ny + kTY3 - 1) / kTY3);
     dim3 grid(tiles, nchunks);
-    step3d_kernel<kTX3, kTY3, kStages3><<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    FD_STEP3D<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
 }
 

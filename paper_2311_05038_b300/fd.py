@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfd.so")
+# FD_LIBRARY selects another build of the same library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("FD_LIBRARY") or os.path.join(_HERE, "libfd.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libfd.so is not built ({LIB_PATH}); run `python -m paper_2311_05038_b300.build`")
