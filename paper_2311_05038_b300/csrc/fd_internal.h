@@ -14,10 +14,10 @@ constexpr int kRadius = 4;
 // along z through bz planes, fed by two TMA rings in shared memory.
 // Compile-time knobs (defaults are the tuned configuration).
 #ifndef FD_TX3
-#define FD_TX3 64
+#define FD_TX3 32
 #endif
 #ifndef FD_TY3
-#define FD_TY3 16
+#define FD_TY3 32
 #endif
 #ifndef FD_STAGESP3
 #define FD_STAGESP3 11

@@ -16,6 +16,7 @@
 // does not act as a spurious mass term that drifts the phase over many steps.
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fd_internal.h"
 #include "ptx.cuh"
@@ -210,8 +211,9 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     float *const out_col = prm.out + ((size_t)z0 * prm.ny + y) * prm.px + x;
     const size_t plane_stride = (size_t)prm.ny * prm.px;
 
-    // z-neighbour queue: Q[i] holds the thread's 4 points of plane z-4+i.
-    float4 Q[9];
+    // z-neighbour queue, advanced three planes at a time: in the r-th body of a
+    // group of three, Q[i + r] holds the thread's 4 points of plane z-4+i.
+    float4 Q[11];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     }
 
     const float2 M2 = make_float2(-6.0f, -6.0f);
-    const float2 TWO = make_float2(2.0f, 2.0f);
+    const float2 NEG1 = make_float2(-1.0f, -1.0f);
     const float2 C1 = make_float2(prm.c1, prm.c1), C2 = make_float2(prm.c2, prm.c2);
     const float2 C3 = make_float2(prm.c3, prm.c3), C4 = make_float2(prm.c4, prm.c4);
     // ring positions of P stage j+8 (newest), P stage j+4 (plane z) and T stage j
@@ -232,16 +234,20 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     int s4 = 4 % SP;
     int st = 0, pht = 0;
 
-    auto body = [&](int j) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&fullP[s8], ph8, &s_abort) &&
-                                         mbar_wait(&fullT[st], pht, &s_abort));
-        if (!ok)
-            return;
+    auto body = [&](int j, auto rot) {
+        constexpr int R = decltype(rot)::value;
+        // fast path: both stages already landed; else bounded waits
+        if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[s8], ph8) & mbar_try_wait(&fullT[st], pht))) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&fullP[s8], ph8, &s_abort) &&
+                                             mbar_wait(&fullT[st], pht, &s_abort));
+            if (!ok)
+                return;
+        }
         const int z = z0 + j;
         const float azv = azn;
         if (prm.has_sponge && z + 1 < z1)
             azn = prm.az[z + 1];
-        Q[8] = *reinterpret_cast<const float4 *>(sP + s8 * PBOX + cP);
+        Q[8 + R] = *reinterpret_cast<const float4 *>(sP + s8 * PBOX + cP);
         const float *pl = sP + s4 * PBOX + cP;
         const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
         const float4 xc = *reinterpret_cast<const float4 *>(pl);
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
         const float4 old = *reinterpret_cast<const float4 *>(sT + (2 * st) * TBOX + cT);
         const float4 wv = *reinterpret_cast<const float4 *>(sT + (2 * st + 1) * TBOX + cT);
         const float xa[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
-        const float4 &pc = Q[4];
+        const float4 &pc = Q[4 + R];
 
         // L'P for the points (0,1) and (2,3) with packed FP32 arithmetic, in the
         // same rounding order as update_point<3>
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
             for (int k = 1; k <= 4; ++k) {
                 const float2 sx = xpair2(xa, h, k);
                 const float2 sy = __fadd2_rn(half2of(yp[k - 1], h), half2of(ym[k - 1], h));
-                const float2 sz = __fadd2_rn(half2of(Q[4 + k], h), half2of(Q[4 - k], h));
+                const float2 sz = __fadd2_rn(half2of(Q[4 + k + R], h), half2of(Q[4 - k + R], h));
                 const float2 d = __ffma2_rn(M2, p2, __fadd2_rn(__fadd2_rn(sx, sy), sz));
                 const float2 ck = k == 1 ? C1 : k == 2 ? C2 : k == 3 ? C3 : C4;
                 a2 = k == 1 ? __fmul2_rn(ck, d) : __ffma2_rn(ck, d, a2);
@@ -276,41 +282,42 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
             acc[h] = a2;
         }
 
-        float pn[4];
         const float ayz = ayv + azv;
+        float2 r[2];
         if (x_band || ayz != 0.f) {
             // sponge band: (w L'P + 2P - (1 - a) Pold) / (1 + a), scalar
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float a = axv[e] + ayz;
-                const float lap = e == 0 ? acc[0].x : e == 1 ? acc[0].y : e == 2 ? acc[1].x : acc[1].y;
-                const float num = fmaf(f4c(wv, e), lap, fmaf(2.0f, f4c(pc, e), -(1.0f - a) * f4c(old, e)));
-                pn[e] = a != 0.0f ? num / (1.0f + a) : num;
+            for (int h = 0; h < 2; ++h) {
+                const float2 p2 = half2of(pc, h), o2 = half2of(old, h), w2 = half2of(wv, h);
+                const float a0 = axv[2 * h] + ayz, a1 = axv[2 * h + 1] + ayz;
+                const float n0 = fmaf(w2.x, acc[h].x, fmaf(2.0f, p2.x, -(1.0f - a0) * o2.x));
+                const float n1 = fmaf(w2.y, acc[h].y, fmaf(2.0f, p2.y, -(1.0f - a1) * o2.y));
+                r[h] = make_float2(a0 != 0.0f ? __fdividef(n0, 1.0f + a0) : n0,
+                                   a1 != 0.0f ? __fdividef(n1, 1.0f + a1) : n1);
             }
         } else {
+            // 2P - Pold as fma(-1, Pold, P + P): P + P is exact, one rounding as before
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float2 o = half2of(old, h);
-                const float2 t = __ffma2_rn(TWO, half2of(pc, h), make_float2(-o.x, -o.y));
-                const float2 r = __ffma2_rn(half2of(wv, h), acc[h], t);
-                pn[2 * h] = r.x;
-                pn[2 * h + 1] = r.y;
+                const float2 p2 = half2of(pc, h);
+                const float2 t = __ffma2_rn(NEG1, half2of(old, h), __fadd2_rn(p2, p2));
+                r[h] = __ffma2_rn(half2of(wv, h), acc[h], t);
             }
         }
         if (src_col && z == prm.sz) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (prm.sx - x == e)
-                    pn[e] += prm.src_amp;
+            const int e = prm.sx - x;
+            if (e == 0) r[0].x += prm.src_amp;
+            if (e == 1) r[0].y += prm.src_amp;
+            if (e == 2) r[1].x += prm.src_amp;
+            if (e == 3) r[1].y += prm.src_amp;
         }
         float *dst = out_col + (size_t)j * plane_stride;
         if (store_vec) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+            *reinterpret_cast<float4 *>(dst) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
         } else if (store_any) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (x + e < prm.nx)
-                    dst[e] = pn[e];
+            dst[0] = r[0].x;
+            if (x + 1 < prm.nx) dst[1] = r[0].y;
+            if (x + 2 < prm.nx) dst[2] = r[1].x;
         }
         release(j + 4, s4, j, st);
         if (++s8 == SP) {
@@ -325,11 +332,15 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
         }
     };
 
-    for (int j = 0; ok && j < nb; ++j) {
-        body(j);
+    for (int jb = 0; ok && jb < nb; jb += 3) {
+        body(jb, std::integral_constant<int, 0>{});
+        if (ok && jb + 1 < nb)
+            body(jb + 1, std::integral_constant<int, 1>{});
+        if (ok && jb + 2 < nb)
+            body(jb + 2, std::integral_constant<int, 2>{});
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            Q[k] = Q[k + 1];
+            Q[k] = Q[k + 3];
     }
     if (ok) {
         for (int k = nb + 4; k < nb + 8; ++k)
