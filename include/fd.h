@@ -159,6 +159,51 @@ fd_status fd_get_source_index(fd_model *m, int64_t *idx);
 fd_status fd_get_receiver_indices(fd_model *m, int64_t *out, int cap);
 fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
 
+/* ----------------------------------------------------------------- batches
+ *
+ * A batch advances many independent 2D shots (models) in one persistent,
+ * cooperative kernel launch instead of one launch per shot and time step.  The
+ * paper has no batching: this is the multi-shot form of the same time step
+ * (section 7, Listing 3), with identical arithmetic, so every shot's
+ * wavefield and traces are bitwise the same alone (fd_step) and in a batch.
+ *
+ * Work items are (shot, tile) pairs.  Each tile keeps a completed-step
+ * counter in device memory; a tile starts step k + 1 only when it and its four
+ * neighbours have completed step k (all waits are bounded; on expiry the
+ * launch stops and fd_batch_step returns FD_ETIMEOUT).  Shots are advanced in
+ * groups whose fields fit a stated budget, so a group stays in the 126 MB L2
+ * across its time steps.  One launch advances every shot by up to
+ * steps_per_launch steps; a run replays one captured CUDA graph node.
+ *
+ * The models stay owned by the caller and must outlive the batch.  A batch
+ * call waits for the models' streams, runs on a stream of the batch's own and
+ * returns when the work is done; meanwhile the models must not be used
+ * otherwise. */
+typedef struct fd_batch fd_batch;
+
+typedef struct fd_batch_tuning {
+    int tile;              /* tile shape: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 (x by z) */
+    int steps_per_launch;  /* time steps per persistent launch, >= 1                       */
+    int ctas_per_sm;       /* resident CTAs per SM, 0 = as many as fit                      */
+    int group_mb;          /* L2 budget per shot group in MB, 0 = all shots in one group    */
+} fd_batch_tuning;
+
+/* Build a batch over nmodels 2D models on the same device (FD_EINVAL for 3D
+ * models, NULL entries or a repeated model). */
+fd_status fd_batch_create(fd_model *const *models, int nmodels, fd_batch **out);
+fd_status fd_batch_destroy(fd_batch *b);
+/* Set / read the tuning (validated; FD_EINVAL for out-of-range values). */
+fd_status fd_batch_set_tuning(fd_batch *b, const fd_batch_tuning *t);
+fd_status fd_batch_get_tuning(fd_batch *b, fd_batch_tuning *t);
+/* Advance shot i by nsteps_each[i] steps (or every shot by nsteps when
+ * nsteps_each is NULL), exactly as fd_step would, traces included.  Blocks
+ * until done; returns FD_ETIMEOUT if a bounded device wait gave up. */
+fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each);
+/* Time every tuning candidate on trial_steps steps of this batch, keep the
+ * fastest (cached per batch shape for the process) and write it to best.  The
+ * trial steps change the models' state: call fd_reset or fd_run_shot after. */
+fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best);
+
 /* Number of CUDA kernel launches this library has issued since load. */
 uint64_t fd_kernel_launch_count(void);
 

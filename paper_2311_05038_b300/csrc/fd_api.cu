@@ -25,15 +25,16 @@
 
 #include "fd.h"
 #include "fd_internal.h"
+#include "fd_model.h"
 
 using namespace fdk;
 
 // ------------------------------------------------------------------ errors & stats
 
 static thread_local std::string g_last_error;
-static std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> fdk::g_launches{0};
 
-static fd_status fail(fd_status st, const char *fmt, ...)
+fd_status fdk::fail(fd_status st, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -44,19 +45,13 @@ static fd_status fail(fd_status st, const char *fmt, ...)
     return st;
 }
 
-static fd_status cuda_fail(cudaError_t e, const char *what)
+fd_status fdk::cuda_fail(cudaError_t e, const char *what)
 {
     if (e == cudaErrorMemoryAllocation)
         return fail(FD_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
     return fail(FD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define FD_CUDA(call, what)                 \
-    do {                                    \
-        cudaError_t e_ = (call);            \
-        if (e_ != cudaSuccess)              \
-            return cuda_fail(e_, what);     \
-    } while (0)
 
 // --------------------------------------------------------------- stencil weights
 
@@ -114,7 +109,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // FP32 tensor map over a pitched field: rank 2 ([nz][px], extents nx, nz) or
 // rank 3 ([nz][ny][px], extents nx, ny, nz), with the given box.
-static bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by)
+bool fdk::make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by)
 {
     auto fn = encode_fn();
     if (!fn)
@@ -150,48 +145,6 @@ static bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, in
 
 // ------------------------------------------------------------------------ model
 
-struct fd_model {
-    fd_grid_desc d{};
-    int nx = 0, ny = 0, nz = 0, px = 0;
-    size_t rows = 0;       // nz * ny
-    size_t pitched = 0;    // rows * px elements per field
-    size_t npts = 0;       // nz * ny * nx
-    int device = 0;
-    cudaStream_t stream = nullptr;
-
-    float *buf[2] = {nullptr, nullptr};   // the two wavefield levels
-    int cur = 0;                          // buf[cur] = P, buf[cur ^ 1] = Pold
-    float *w = nullptr;
-    float *ax = nullptr, *ay = nullptr, *az = nullptr;
-    int has_sponge = 0;
-    float vmax = 0.f;
-    int *d_err = nullptr;
-    unsigned *d_stats = nullptr;
-
-    CUtensorMap halo_map[2];   // haloed P box over buf[i]
-    CUtensorMap tile_map[2];   // unhaloed box over buf[i] (as Pold)
-    CUtensorMap w_map;
-    int nchunks = 1;           // 3D: CTAs along z
-    int bz = 1;
-
-    int src_on = 0, sx = 0, sy = 0, sz = 0;
-    std::vector<float> amp;    // dt^2 S(t_n) / h^d
-
-    int nrec = 0;
-    int64_t *d_rec = nullptr;  // pitched indices (device)
-    int rec_cap = 0;
-    std::vector<int64_t> rec_dense;
-
-    float *traces = nullptr;
-    int trace_rows = 0;
-    bool traces_owned = false;
-    size_t trace_cap = 0;      // floats in an owned trace buffer
-    float *stage = nullptr;    // velocity staging, kept once fd_set_velocity is used
-
-    int n = 0;
-    int pending_row = -1;      // receiver row whose gather is still owed
-};
-
 static fd_status validate_desc(const fd_grid_desc *d)
 {
     if (!d)
@@ -212,6 +165,13 @@ static fd_status validate_desc(const fd_grid_desc *d)
     if (npts > 4.0e10)
         return fail(FD_EINVAL, "grid of %.3g points is too large", npts);
     return FD_OK;
+}
+
+// Damping profiles are allocated with zero padding past the grid, so that tile
+// slices (up to 128 entries from a tile origin) can be copied without bounds checks.
+static size_t profile_floats(int n)
+{
+    return ((size_t)n + 127) / 128 * 128 + 128;
 }
 
 // Per-axis damping a_i = dt * eta_max * (d_i / W)^2, d_i = max(W - i, i - (n-1-W), 0).
@@ -241,6 +201,7 @@ static void free_model(fd_model *m)
     cudaFree(m->d_err);
     cudaFree(m->d_stats);
     cudaFree(m->d_rec);
+    cudaFree(m->d_amp);
     cudaFree(m->stage);
     if (m->traces_owned)
         cudaFree(m->traces);
@@ -356,9 +317,12 @@ static fd_status create(const fd_grid_desc *desc, const float *v, cudaMemcpyKind
     if ((e = cudaMalloc((void **)&m->buf[0], bytes)) != cudaSuccess ||
         (e = cudaMalloc((void **)&m->buf[1], bytes)) != cudaSuccess ||
         (e = cudaMalloc((void **)&m->w, bytes)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&m->ax, (size_t)m->px * 4)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&m->ay, (size_t)m->ny * 4)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&m->az, (size_t)m->nz * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->ax, profile_floats(m->px) * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->ay, profile_floats(m->ny) * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&m->az, profile_floats(m->nz) * 4)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->ax, 0, profile_floats(m->px) * 4, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->ay, 0, profile_floats(m->ny) * 4, m->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(m->az, 0, profile_floats(m->nz) * 4, m->stream)) != cudaSuccess ||
         (e = cudaMalloc((void **)&m->d_err, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc((void **)&m->d_stats, 2 * sizeof(unsigned))) != cudaSuccess)
         return bail(cuda_fail(e, "device allocation"));
@@ -457,8 +421,7 @@ static bool inside(const fd_model *m, int ix, int iy, int iz)
 
 extern "C" fd_status fd_set_source(fd_model *m, int ix, int iy, int iz, const float *wavelet_host, int nt)
 {
-    if (!m)
-        return fail(FD_EINVAL, "NULL model");
+    NEED_MODEL(m);
     if (nt < 0)
         return fail(FD_EINVAL, "nt must be >= 0");
     if (m->d.ndim == 2)
@@ -474,6 +437,17 @@ extern "C" fd_status fd_set_source(fd_model *m, int ix, int iy, int iz, const fl
     std::vector<float> amp(nt);
     for (int i = 0; i < nt; ++i)
         amp[i] = (float)(m->d.dt * m->d.dt * (double)wavelet_host[i] / hd);
+    if (nt > m->amp_cap) {
+        float *p = nullptr;
+        FD_CUDA(cudaMalloc((void **)&p, (size_t)nt * sizeof(float)), "source allocation");
+        cudaStreamSynchronize(m->stream);
+        cudaFree(m->d_amp);
+        m->d_amp = p;
+        m->amp_cap = nt;
+    }
+    FD_CUDA(cudaMemcpyAsync(m->d_amp, amp.data(), (size_t)nt * sizeof(float), cudaMemcpyHostToDevice, m->stream),
+            "source upload");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "source upload");
     m->amp.swap(amp);
     m->src_on = 1;
     m->sx = ix;

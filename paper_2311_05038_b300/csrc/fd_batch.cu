@@ -1,0 +1,756 @@
+// fd_batch.cu -- many 2D shots in one persistent, dependency-driven launch.
+//
+// The time step is the one of fd_kernels.cu (the paper's section 7 routine
+// sequence, fused); what changes is the schedule.  Instead of one launch per
+// shot and time step, one cooperative launch of resident CTAs walks a table of
+// work items (shot, tile).  Each item keeps a completed-step counter in global
+// memory: a tile may compute step k+1 once it and its four neighbours have
+// completed step k.  That single rule orders both hazards of the two rotating
+// buffers: the halo it reads (written by the neighbours at step k) and the
+// region it overwrites (read as halo by the neighbours at step k).
+//
+// Inside a CTA one producer lane waits on the counters (bounded spins), then
+// issues the TMA loads of the haloed P tile and the Pold and w tiles into a
+// ring of stages; the consumer warps compute the tile with the shared arithmetic
+// of stencil.cuh, write Pn, the tile's receivers and the source, and publish
+// the counter with release semantics.  Items are visited group by group; all
+// time steps of a launch are done on one group before the next, so a group
+// whose fields fit in L2 stays resident while it steps.
+//
+// The launch carries no per-launch arguments: the step base is a counter in
+// device memory advanced by the last CTA to finish, so one captured graph node
+// is replayed until every shot has reached its target.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fd.h"
+#include "fd_internal.h"
+#include "fd_model.h"
+#include "ptx.cuh"
+#include "stencil.cuh"
+
+namespace fdk {
+
+struct ShotDesc {
+    CUtensorMap halo[2];   // haloed P box over buf[i]
+    CUtensorMap tile[2];   // tile box over buf[i] (as Pold)
+    CUtensorMap wmap;
+    float *buf[2];
+    const float *ax, *az;
+    const float *amp;      // dt^2 S(t_n) / h^2 per absolute step
+    float *traces;
+    int namp, trace_rows, nrec;
+    int nx, nz, px;
+    int n0, cur0, target, has_sponge;
+    int src_on, sx, sz;
+};
+
+struct BatchItem {
+    int shot, x0, z0;
+    int nb[4];             // neighbour items (left, right, up, down), -1 at the grid edge
+    int rec_begin, rec_end;
+};
+
+struct BatchRec {
+    int local;             // (z - z0) * TX + (x - x0) within the tile
+    int r;                 // receiver index of the shot
+};
+
+struct BatchState {
+    int launch;            // launches completed in the current run
+    unsigned done;         // CTAs finished in the current launch
+};
+
+struct BatchParams {
+    const ShotDesc *shots;
+    const BatchItem *items;
+    const BatchRec *recs;
+    int *counters;         // per item: steps completed in the current run
+    const int *group_begin;
+    int ngroups;
+    int K;                 // steps per launch
+    BatchState *state;
+    float c1, c2, c3, c4;
+    int *err;
+};
+
+// What the consumers need about the item in a ring stage; written by the
+// producer before it arms the stage's barrier, so consumers read only shared
+// memory.  item < 0 marks the end of the work.
+struct StageMeta {
+    float *out;            // Pn destination (the shot's Pold buffer)
+    float *trace_row;      // traces + n * nrec, or null when no row is recorded
+    int item, x0, z0, nx, nz, px;
+    int rec_begin, rec_end;
+    int src_local;         // the source's (z - z0) * TX + (x - x0), or -1
+    float src_amp;
+    int has_sponge;
+    int cs;                // the step this stage computes (run-relative)
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Order this thread's earlier generic-proxy accesses (the acquire of a
+// neighbour's counter) before its later async-proxy (TMA) reads of global memory.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until item i and its neighbours have completed v steps: the five
+// counters are read together (independent relaxed loads), and one acquire
+// fence orders the later reads after them.  False if the cycle budget runs
+// out or *abort is raised.
+__device__ __forceinline__ bool wait_deps(const int *counters, int i, const int (&nb)[4], int v,
+                                          volatile int *abort)
+{
+    long long t0 = -1;
+    for (;;) {
+        const int c0 = ld_relaxed(&counters[i]);
+        const int c1 = nb[0] >= 0 ? ld_relaxed(&counters[nb[0]]) : v;
+        const int c2 = nb[1] >= 0 ? ld_relaxed(&counters[nb[1]]) : v;
+        const int c3 = nb[2] >= 0 ? ld_relaxed(&counters[nb[2]]) : v;
+        const int c4 = nb[3] >= 0 ? ld_relaxed(&counters[nb[3]]) : v;
+        if (min(min(c0, c1), min(min(c2, c3), c4)) >= v)
+            break;
+        if (t0 < 0)
+            t0 = clock64();
+        else if (*abort || clock64() - t0 > kWaitLimitCycles)
+            return false;
+        __nanosleep(32);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return true;
+}
+
+template <int TX, int TZ, int S>
+__global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchParams bp)
+{
+    constexpr int QX = TX / 4;
+    constexpr int NC = QX * TZ;
+    constexpr int NCW = NC / 32;
+    constexpr int HX = TX + 8;
+    constexpr int HZ = TZ + 8;
+    constexpr int PBOX = HX * HZ;
+    constexpr int TBOX = TX * TZ;
+    constexpr uint32_t BYTES = (PBOX + 2 * TBOX) * 4;
+    static_assert(NC % 32 == 0, "consumers must fill warps");
+    static_assert((PBOX * 4) % 128 == 0 && (TBOX * 4) % 128 == 0, "boxes keep 128-byte alignment");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sP = reinterpret_cast<float *>(smem);
+    float *sO = sP + S * PBOX;
+    float *sW = sO + S * TBOX;
+    float *sAx = sW + S * TBOX;             // [S][TX] sponge slice along x
+    float *sAz = sAx + S * TX;              // [S][TZ] sponge slice along z
+    float *sPn = sAz + S * TZ;              // [TBOX] results, for the receivers
+    uint64_t *full = reinterpret_cast<uint64_t *>(sPn + TBOX);
+    uint64_t *empty = full + S;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(empty + S);
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int launch = *reinterpret_cast<volatile int *>(&bp.state->launch);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int k = 0;
+            bool good = true;
+            for (int g = 0; good && g < bp.ngroups; ++g) {
+                const int ib = bp.group_begin[g], ie = bp.group_begin[g + 1];
+                for (int sw = 0; good && sw < bp.K; ++sw) {
+                    const int cs = launch * bp.K + sw;
+                    BatchItem nxt;
+                    if (ib + (int)blockIdx.x < ie)
+                        nxt = bp.items[ib + blockIdx.x];
+                    for (int i = ib + blockIdx.x; i < ie; i += gridDim.x) {
+                        const BatchItem it = nxt;
+                        if (i + (int)gridDim.x < ie)
+                            nxt = bp.items[i + gridDim.x];   // prefetch the next descriptor
+                        const ShotDesc &sd = bp.shots[it.shot];
+                        if (cs >= sd.target)
+                            continue;
+                        good = wait_deps(bp.counters, i, it.nb, cs, &s_abort);
+                        const int slot = k % S;
+                        if (good && k >= S)
+                            good = mbar_wait(&empty[slot], ((k / S) - 1) & 1, &s_abort);
+                        if (!good)
+                            break;
+                        fence_proxy_async_global();
+                        const int pb = (sd.cur0 + cs) & 1;
+                        const int n = sd.n0 + cs;
+                        StageMeta &mt = meta[slot];
+                        mt.out = sd.buf[pb ^ 1];
+                        mt.trace_row = (it.rec_begin < it.rec_end && n < sd.trace_rows)
+                                           ? sd.traces + (size_t)n * sd.nrec
+                                           : nullptr;
+                        mt.item = i;
+                        mt.cs = cs;
+                        mt.x0 = it.x0;
+                        mt.z0 = it.z0;
+                        mt.nx = sd.nx;
+                        mt.nz = sd.nz;
+                        mt.px = sd.px;
+                        mt.rec_begin = it.rec_begin;
+                        mt.rec_end = it.rec_end;
+                        const bool src_here = sd.src_on && n < sd.namp && sd.sx >= it.x0 && sd.sx < it.x0 + TX &&
+                                              sd.sz >= it.z0 && sd.sz < it.z0 + TZ;
+                        mt.src_local = src_here ? (sd.sz - it.z0) * TX + (sd.sx - it.x0) : -1;
+                        mt.src_amp = src_here ? sd.amp[n] : 0.f;
+                        mt.has_sponge = sd.has_sponge;
+                        mbar_arrive_expect_tx(&full[slot], BYTES + (sd.has_sponge ? (TX + TZ) * 4 : 0));
+                        tma_load_2d(sP + slot * PBOX, &sd.halo[pb], &full[slot], it.x0 - 4, it.z0 - 4);
+                        tma_load_2d(sO + slot * TBOX, &sd.tile[pb ^ 1], &full[slot], it.x0, it.z0);
+                        tma_load_2d(sW + slot * TBOX, &sd.wmap, &full[slot], it.x0, it.z0);
+                        if (sd.has_sponge) {
+                            bulk_load(sAx + slot * TX, sd.ax + it.x0, TX * 4, &full[slot]);
+                            bulk_load(sAz + slot * TZ, sd.az + it.z0, TZ * 4, &full[slot]);
+                        }
+                        ++k;
+                    }
+                }
+            }
+            const int slot = k % S;
+            if (good && (k < S || mbar_wait(&empty[slot], ((k / S) - 1) & 1, &s_abort))) {
+                // end marker for the consumers (every issued stage is waited on by
+                // them before the CTA can exit, so no copy outlives the CTA)
+                meta[slot].item = -1;
+                mbar_arrive(&full[slot]);
+            } else {
+                // abort: consumers leave on the flag; stay until the copies into
+                // this CTA's shared memory have landed (bounded)
+                raise_error(bp.err, &s_abort, kDevErrTimeout);
+                int never = 0;
+                for (int q = max(0, k - S); q < k; ++q)
+                    mbar_wait(&full[q % S], (q / S) & 1, &never, kWaitLimitCycles / 8);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int tx = tid % QX;
+        const int tz = tid / QX;
+        for (int k = 0;; ++k) {
+            const int slot = k % S;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (k / S) & 1, &s_abort))) {
+                raise_error(bp.err, &s_abort, kDevErrTimeout);
+                break;
+            }
+            const StageMeta &mt = meta[slot];
+            const int item = mt.item;
+            if (item < 0)
+                break;
+            const int x = mt.x0 + 4 * tx;
+            const int z = mt.z0 + tz;
+            float axv[4] = {0.f, 0.f, 0.f, 0.f};
+            float azv = 0.f;
+            if (mt.has_sponge) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(sAx + slot * TX + 4 * tx);
+                axv[0] = a4.x;
+                axv[1] = a4.y;
+                axv[2] = a4.z;
+                axv[3] = a4.w;
+                azv = sAz[slot * TZ + tz];
+            }
+            float2 r[2];
+            tile2d_update<TX>(sP + slot * PBOX, sO + slot * TBOX, sW + slot * TBOX, tx, tz, axv, azv, bp.c1, bp.c2,
+                              bp.c3, bp.c4, r);
+            const int local = tz * TX + 4 * tx;
+            if ((unsigned)(mt.src_local - local) < 4u)
+                add_source4(r, mt.src_local - local, mt.src_amp);
+            if (z < mt.nz && x < mt.nx)
+                store4(mt.out + (size_t)z * mt.px + x, r, mt.nx - x);
+            if (mt.rec_begin < mt.rec_end) {
+                *reinterpret_cast<float4 *>(sPn + local) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+                named_sync(1, NC);
+                if (mt.trace_row)
+                    for (int q = mt.rec_begin + tid; q < mt.rec_end; q += NC)
+                        mt.trace_row[bp.recs[q].r] = sPn[bp.recs[q].local];
+            }
+            named_sync(1, NC);
+            if (tid == 0) {
+                __threadfence();
+                st_release(&bp.counters[item], mt.cs + 1);
+                mbar_arrive(&empty[slot]);
+            }
+        }
+    }
+
+    // the last CTA to finish advances the launch counter for the next replay
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&bp.state->done, 1u) == gridDim.x - 1) {
+            bp.state->done = 0;
+            bp.state->launch = launch + 1;
+            __threadfence();
+        }
+    }
+}
+
+// Compiled tile variants: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16.
+constexpr int kBatchStages = 3;
+struct Variant {
+    int tx, tz;
+    const void *fn;
+    int threads;
+    size_t smem;
+};
+
+template <int TX, int TZ>
+static Variant variant()
+{
+    constexpr int PBOX = (TX + 8) * (TZ + 8);
+    constexpr int TBOX = TX * TZ;
+    const size_t smem = (size_t)(kBatchStages * (PBOX + 2 * TBOX + TX + TZ) + TBOX) * 4 + 2 * kBatchStages * 8 +
+                        kBatchStages * sizeof(StageMeta);
+    return Variant{TX, TZ, (const void *)batch2d_kernel<TX, TZ, kBatchStages>, TX / 4 * TZ + 32, smem};
+}
+
+static Variant get_variant(int tile)
+{
+    switch (tile) {
+    case 1:
+        return variant<64, 32>();
+    case 2:
+        return variant<128, 16>();
+    default:
+        return variant<64, 16>();
+    }
+}
+
+}  // namespace fdk
+
+using namespace fdk;
+
+// ------------------------------------------------------------------------ host
+
+struct fd_batch {
+    std::vector<fd_model *> models;
+    int device = 0;
+    cudaStream_t stream = nullptr;   // owned by the batch
+    fd_batch_tuning tun{0, 2000, 0, 96};
+    bool built = false;     // tables match the tuning
+    ShotDesc *d_shots = nullptr;
+    BatchItem *d_items = nullptr;
+    BatchRec *d_recs = nullptr;
+    int *d_counters = nullptr;
+    int *d_group = nullptr;
+    BatchState *d_state = nullptr;
+    int *d_err = nullptr;
+    int nitems = 0, ngroups = 0, grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ShotDesc> shots;   // host copy (tensor maps, pointers)
+};
+
+static void free_tables(fd_batch *b)
+{
+    cudaFree(b->d_shots);
+    cudaFree(b->d_items);
+    cudaFree(b->d_recs);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_group);
+    b->d_shots = nullptr;
+    b->d_items = nullptr;
+    b->d_recs = nullptr;
+    b->d_counters = nullptr;
+    b->d_group = nullptr;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->built = false;
+}
+
+// Build the item table, receiver lists, groups and per-shot descriptors for
+// the current tuning (shot-dependent fields n0 / cur0 / target are set per run).
+static fd_status build_tables(fd_batch *b)
+{
+    free_tables(b);
+    const Variant v = get_variant(b->tun.tile);
+    std::vector<BatchItem> items;
+    std::vector<BatchRec> recs;
+    std::vector<int> group{0};
+    const double budget = b->tun.group_mb > 0 ? b->tun.group_mb * 1048576.0 : 1e300;
+    double in_group = 0.0;
+    b->shots.assign(b->models.size(), ShotDesc{});
+    for (size_t s = 0; s < b->models.size(); ++s) {
+        fd_model *m = b->models[s];
+        ShotDesc &d = b->shots[s];
+        bool ok = true;
+        for (int i = 0; i < 2; ++i) {
+            ok = ok && make_map(&d.halo[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, v.tx + 8, v.tz + 8);
+            ok = ok && make_map(&d.tile[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, v.tx, v.tz);
+            d.buf[i] = m->buf[i];
+        }
+        ok = ok && make_map(&d.wmap, m->w, 2, m->nx, 1, m->nz, m->px, v.tx, v.tz);
+        if (!ok)
+            return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed for batch shot %zu", s);
+        d.ax = m->ax;
+        d.az = m->az;
+        d.nx = m->nx;
+        d.nz = m->nz;
+        d.px = m->px;
+        d.has_sponge = m->has_sponge;
+        // shot grouping by field bytes (P, Pold, w)
+        const double bytes = 3.0 * m->pitched * sizeof(float);
+        if (s > 0 && in_group + bytes > budget) {
+            group.push_back((int)items.size());
+            in_group = 0.0;
+        }
+        in_group += bytes;
+        // tiles of this shot, row-major; neighbours are items of the same shot
+        const int tx_n = (m->nx + v.tx - 1) / v.tx, tz_n = (m->nz + v.tz - 1) / v.tz;
+        const int base = (int)items.size();
+        std::vector<std::vector<BatchRec>> tile_recs((size_t)tx_n * tz_n);
+        for (int r = 0; r < m->nrec; ++r) {
+            const int64_t di = m->rec_dense[r];
+            const int ix = (int)(di % m->nx), iz = (int)(di / m->nx);
+            const int t = (iz / v.tz) * tx_n + ix / v.tx;
+            tile_recs[t].push_back(BatchRec{(iz % v.tz) * v.tx + ix % v.tx, r});
+        }
+        for (int tz = 0; tz < tz_n; ++tz)
+            for (int tx = 0; tx < tx_n; ++tx) {
+                BatchItem it{};
+                it.shot = (int)s;
+                it.x0 = tx * v.tx;
+                it.z0 = tz * v.tz;
+                it.nb[0] = tx > 0 ? base + tz * tx_n + tx - 1 : -1;
+                it.nb[1] = tx + 1 < tx_n ? base + tz * tx_n + tx + 1 : -1;
+                it.nb[2] = tz > 0 ? base + (tz - 1) * tx_n + tx : -1;
+                it.nb[3] = tz + 1 < tz_n ? base + (tz + 1) * tx_n + tx : -1;
+                const auto &tr = tile_recs[(size_t)tz * tx_n + tx];
+                it.rec_begin = (int)recs.size();
+                recs.insert(recs.end(), tr.begin(), tr.end());
+                it.rec_end = (int)recs.size();
+                items.push_back(it);
+            }
+    }
+    group.push_back((int)items.size());
+    b->nitems = (int)items.size();
+    b->ngroups = (int)group.size() - 1;
+    FD_CUDA(cudaMalloc((void **)&b->d_shots, b->shots.size() * sizeof(ShotDesc)), "batch allocation");
+    FD_CUDA(cudaMalloc((void **)&b->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem)), "batch allocation");
+    FD_CUDA(cudaMalloc((void **)&b->d_recs, std::max<size_t>(1, recs.size()) * sizeof(BatchRec)), "batch allocation");
+    FD_CUDA(cudaMalloc((void **)&b->d_counters, std::max(1, b->nitems) * sizeof(int)), "batch allocation");
+    FD_CUDA(cudaMalloc((void **)&b->d_group, group.size() * sizeof(int)), "batch allocation");
+    FD_CUDA(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice), "batch upload");
+    if (!recs.empty())
+        FD_CUDA(cudaMemcpy(b->d_recs, recs.data(), recs.size() * sizeof(BatchRec), cudaMemcpyHostToDevice), "batch upload");
+    FD_CUDA(cudaMemcpy(b->d_group, group.data(), group.size() * sizeof(int), cudaMemcpyHostToDevice), "batch upload");
+
+    // resident grid
+    FD_CUDA(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem), "kernel attributes");
+    int per_sm = 0, sms = 0;
+    FD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.threads, v.smem), "occupancy");
+    FD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device attribute");
+    if (per_sm < 1)
+        return fail(FD_ECUDA, "batch kernel does not fit on an SM");
+    if (b->tun.ctas_per_sm > 0)
+        per_sm = std::min(per_sm, b->tun.ctas_per_sm);
+    b->grid = sms * per_sm;
+    b->built = true;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_create(fd_model *const *models, int nmodels, fd_batch **out)
+{
+    if (!out || !models || nmodels < 1)
+        return fail(FD_EINVAL, "fd_batch_create: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < nmodels; ++i) {
+        if (!models[i])
+            return fail(FD_EINVAL, "fd_batch_create: model %d is NULL", i);
+        if (models[i]->d.ndim != 2)
+            return fail(FD_EINVAL, "fd_batch_create: model %d is not 2D", i);
+        if (models[i]->device != models[0]->device)
+            return fail(FD_EINVAL, "fd_batch_create: models on different devices");
+        for (int j = 0; j < i; ++j)
+            if (models[j] == models[i])
+                return fail(FD_EINVAL, "fd_batch_create: model %d repeated", i);
+    }
+    fd_batch *b = new fd_batch();
+    b->models.assign(models, models + nmodels);
+    b->device = models[0]->device;
+    cudaError_t e = cudaSetDevice(b->device);
+    // a stream of its own: the launch is captured into a graph, which the
+    // legacy default stream does not allow
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_state, sizeof(BatchState));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        fd_batch_destroy(b);
+        return cuda_fail(e, "batch allocation");
+    }
+    *out = b;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_destroy(fd_batch *b)
+{
+    if (!b)
+        return FD_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    free_tables(b);
+    cudaFree(b->d_state);
+    cudaFree(b->d_err);
+    if (b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_set_tuning(fd_batch *b, const fd_batch_tuning *t)
+{
+    if (!b || !t)
+        return fail(FD_EINVAL, "fd_batch_set_tuning: NULL argument");
+    if (t->tile < 0 || t->tile > 2 || t->steps_per_launch < 1 || t->ctas_per_sm < 0 || t->group_mb < 0)
+        return fail(FD_EINVAL, "fd_batch_set_tuning: value out of range");
+    const bool same = t->tile == b->tun.tile && t->ctas_per_sm == b->tun.ctas_per_sm && t->group_mb == b->tun.group_mb;
+    b->tun = *t;
+    if (!same)
+        free_tables(b);
+    else if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_get_tuning(fd_batch *b, fd_batch_tuning *t)
+{
+    if (!b || !t)
+        return fail(FD_EINVAL, "fd_batch_get_tuning: NULL argument");
+    *t = b->tun;
+    return FD_OK;
+}
+
+static fd_status capture_graph(fd_batch *b, const BatchParams &p)
+{
+    const Variant v = get_variant(b->tun.tile);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(v.threads);
+    cfg.dynamicSmemBytes = v.smem;
+    cfg.stream = b->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&p};
+    cudaGraph_t graph = nullptr;
+    FD_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    cudaError_t e = cudaLaunchKernelExC(&cfg, v.fn, args);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return cuda_fail(e != cudaSuccess ? e : e2, "batch kernel capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "graph instantiate");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each)
+{
+    if (!b)
+        return fail(FD_EINVAL, "NULL batch");
+    FD_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    if (!nsteps_each && nsteps < 0)
+        return fail(FD_EINVAL, "nsteps must be >= 0");
+    const size_t ns = b->models.size();
+    std::vector<int> target(ns);
+    int tmax = 0;
+    for (size_t s = 0; s < ns; ++s) {
+        target[s] = nsteps_each ? nsteps_each[s] : nsteps;
+        if (target[s] < 0)
+            return fail(FD_EINVAL, "negative step count for shot %zu", s);
+        tmax = std::max(tmax, target[s]);
+    }
+    if (!b->built) {
+        fd_status st = build_tables(b);
+        if (st)
+            return st;
+    }
+    // the models' own streams must be idle before the batch uses their buffers
+    for (fd_model *m : b->models)
+        FD_CUDA(cudaStreamSynchronize(m->stream), "model stream");
+    for (size_t s = 0; s < ns; ++s) {
+        fd_model *m = b->models[s];
+        ShotDesc &d = b->shots[s];
+        d.amp = m->d_amp;
+        d.namp = m->src_on ? (int)m->amp.size() : 0;
+        d.src_on = m->src_on;
+        d.sx = m->sx;
+        d.sz = m->sz;
+        d.traces = m->nrec > 0 ? m->traces : nullptr;
+        d.trace_rows = d.traces ? m->trace_rows : 0;
+        d.nrec = m->nrec;
+        d.n0 = m->n;
+        d.cur0 = m->cur;
+        d.target = target[s];
+        d.has_sponge = m->has_sponge;
+    }
+    FD_CUDA(cudaMemcpyAsync(b->d_shots, b->shots.data(), ns * sizeof(ShotDesc), cudaMemcpyHostToDevice, b->stream),
+            "batch upload");
+    FD_CUDA(cudaMemsetAsync(b->d_counters, 0, std::max(1, b->nitems) * sizeof(int), b->stream), "batch reset");
+    FD_CUDA(cudaMemsetAsync(b->d_state, 0, sizeof(BatchState), b->stream), "batch reset");
+    if (tmax > 0) {
+        if (!b->exec) {
+            float w4[4];
+            fd_stencil_weights(w4);
+            BatchParams p{};
+            p.shots = b->d_shots;
+            p.items = b->d_items;
+            p.recs = b->d_recs;
+            p.counters = b->d_counters;
+            p.group_begin = b->d_group;
+            p.ngroups = b->ngroups;
+            p.K = b->tun.steps_per_launch;
+            p.state = b->d_state;
+            p.c1 = w4[0];
+            p.c2 = w4[1];
+            p.c3 = w4[2];
+            p.c4 = w4[3];
+            p.err = b->d_err;
+            fd_status st = capture_graph(b, p);
+            if (st)
+                return st;
+        }
+        const int launches = (tmax + b->tun.steps_per_launch - 1) / b->tun.steps_per_launch;
+        for (int l = 0; l < launches; ++l) {
+            FD_CUDA(cudaGraphLaunch(b->exec, b->stream), "batch launch");
+            ++g_launches;
+        }
+    }
+    FD_CUDA(cudaStreamSynchronize(b->stream), "batch run");
+    int err = 0;
+    FD_CUDA(cudaMemcpy(&err, b->d_err, sizeof err, cudaMemcpyDeviceToHost), "error word");
+    for (size_t s = 0; s < ns; ++s) {
+        fd_model *m = b->models[s];
+        m->n += target[s];
+        m->cur ^= target[s] & 1;
+        m->pending_row = -1;
+    }
+    if (err) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return fail(FD_ETIMEOUT, "a batch dependency wait gave up (device code %d)", err);
+    }
+    return FD_OK;
+}
+
+namespace {
+std::map<std::string, fd_batch_tuning> g_tuning_cache;
+
+std::string batch_signature(const fd_batch *b)
+{
+    std::string sig;
+    for (const fd_model *m : b->models)
+        sig += std::to_string(m->nx) + "x" + std::to_string(m->nz) + (m->has_sponge ? "s" : "") + ";";
+    return sig;
+}
+}  // namespace
+
+extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best)
+{
+    if (!b || trial_steps < 1)
+        return fail(FD_EINVAL, "fd_batch_autotune: bad arguments");
+    const std::string sig = batch_signature(b) + "/" + std::to_string(trial_steps);
+    auto hit = g_tuning_cache.find(sig);
+    if (hit != g_tuning_cache.end()) {
+        fd_status st = fd_batch_set_tuning(b, &hit->second);
+        if (best)
+            *best = hit->second;
+        return st;
+    }
+    double total_mb = 0;
+    for (const fd_model *m : b->models)
+        total_mb += 3.0 * m->pitched * 4 / 1048576.0;
+    std::vector<int> groups{0};
+    for (int g : {24, 48, 96})
+        if (g < total_mb)
+            groups.push_back(g);
+    const int keep_k = b->tun.steps_per_launch;
+    fd_batch_tuning best_t = b->tun;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    FD_CUDA(cudaEventCreate(&e0), "event");
+    FD_CUDA(cudaEventCreate(&e1), "event");
+    for (int tile = 0; tile < 3; ++tile)
+        for (int g : groups)
+            for (int cps : {0, 2}) {
+                fd_batch_tuning t{tile, trial_steps, cps, g};
+                fd_status st = fd_batch_set_tuning(b, &t);
+                if (!st)
+                    st = fd_batch_step(b, 1, nullptr);   // build, capture and warm up
+                if (st)
+                    continue;
+                cudaEventRecord(e0, b->stream);
+                st = fd_batch_step(b, trial_steps, nullptr);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (!st && ms < best_ms) {
+                    best_ms = ms;
+                    best_t = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f)
+        return fail(FD_ECUDA, "fd_batch_autotune: no candidate ran");
+    best_t.steps_per_launch = keep_k;   // the trials time throughput; the caller's step granularity stays
+    g_tuning_cache[sig] = best_t;
+    if (best)
+        *best = best_t;
+    return fd_batch_set_tuning(b, &best_t);
+}

@@ -1,10 +1,13 @@
 // fd_internal.h -- parameters and launchers shared by the host API and the kernels.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include "fd.h"
 
 namespace fdk {
 
@@ -78,5 +81,22 @@ cudaError_t launch_velocity_stats(const float *v, int nx, size_t rows, int px, u
 // w = (dt/h * v)^2 rounded to FP32 over the pitched layout (v may alias w).
 cudaError_t launch_compute_w(const float *v, float *w, int nx, size_t rows, int px, double dt_over_h,
                              cudaStream_t s);
+
+// Host helpers shared by the C ABI translation units.
+// FP32 tensor map over a pitched field: rank 2 ([nz][px], extents nx, nz) or
+// rank 3 ([nz][ny][px], extents nx, ny, nz), with box bx x by (x 1).
+bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by);
+// Record a message for fd_last_error() and return st.
+fd_status fail(fd_status st, const char *fmt, ...);
+fd_status cuda_fail(cudaError_t e, const char *what);
+extern std::atomic<uint64_t> g_launches;
+
+// Return the fd_status of a failed CUDA call from the enclosing entry point.
+#define FD_CUDA(call, what)                    \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess)                 \
+            return fdk::cuda_fail(e_, what);   \
+    } while (0)
 
 }  // namespace fdk

@@ -7,64 +7,16 @@
 // field passes of the unfused routine sequence.  The receiver gather of the
 // previous step rides along in the same launch.
 //
-// Arithmetic per point (FP32, FMA):
-//   S_k = sum over the axes of (P[+k] + P[-k]),  D_k = S_k - 2d P   (one rounding)
-//   L'P = c1 D_1 + c2 D_2 + c3 D_3 + c4 D_4
-//   Pn  = (w L'P + 2P - (1 - a) Pold) / (1 + a)       (a = 0: no division)
-// Forming D_k before weighting keeps every large-magnitude sum exact or
-// single-rounded, so a constant field gives L'P = 0 exactly and FP32 rounding
-// does not act as a spurious mass term that drifts the phase over many steps.
+// The per-point arithmetic lives in stencil.cuh.
 
 #include <algorithm>
 #include <type_traits>
 
 #include "fd_internal.h"
 #include "ptx.cuh"
+#include "stencil.cuh"
 
 namespace fdk {
-
-__device__ __forceinline__ float f4c(const float4 &v, int e)
-{
-    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-}
-
-__device__ __forceinline__ float2 half2of(const float4 &v, int h)
-{
-    return h == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
-}
-
-// x pair sums P[x+k] + P[x-k] for the two points (2h, 2h+1) of a thread whose
-// row segment x-4 .. x+7 is xa[0..11].  Even k keeps both operands on aligned
-// register pairs (one packed add); odd k straddles them (two scalar adds with
-// the same rounding).
-__device__ __forceinline__ float2 xpair2(const float (&xa)[12], int h, int k)
-{
-    const int i = 4 + 2 * h;
-    if ((k & 1) == 0)
-        return __fadd2_rn(make_float2(xa[i + k], xa[i + k + 1]), make_float2(xa[i - k], xa[i - k + 1]));
-    return make_float2(xa[i + k] + xa[i - k], xa[i + k + 1] + xa[i - k + 1]);
-}
-
-// Damped leapfrog update of one point from its centre value, Pold, w, damping a
-// and the four distance sums S_k over NDIM axes.
-template <int NDIM>
-__device__ __forceinline__ float update_point(const StepParams &prm, float p, float pold, float w,
-                                              float a, float s1, float s2, float s3, float s4)
-{
-    constexpr float m = -2.0f * NDIM;
-    float acc = prm.c1 * fmaf(m, p, s1);
-    acc = fmaf(prm.c2, fmaf(m, p, s2), acc);
-    acc = fmaf(prm.c3, fmaf(m, p, s3), acc);
-    acc = fmaf(prm.c4, fmaf(m, p, s4), acc);
-    const float num = fmaf(w, acc, fmaf(2.0f, p, -(1.0f - a) * pold));
-    return a != 0.0f ? num / (1.0f + a) : num;
-}
-
-__device__ __forceinline__ void raise_error(int *err, volatile int *abort_flag, int code)
-{
-    *abort_flag = 1;
-    atomicCAS(err, 0, code);
-}
 
 // Gather of the previous step's receiver row, spread over every thread of the grid.
 __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
@@ -417,46 +369,12 @@ __global__ void __launch_bounds__(TX / 4 * TZ)
             raise_error(prm.err, &s_abort, kDevErrTimeout);
         return;
     }
-    const float *pl = sP + (tz + 4) * HX + 4 * tx + 4;
-    const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
-    const float4 xc = *reinterpret_cast<const float4 *>(pl);
-    const float4 xp = *reinterpret_cast<const float4 *>(pl + 4);
-    float4 zm[4], zp[4];
-#pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-        zm[k - 1] = *reinterpret_cast<const float4 *>(pl - k * HX);
-        zp[k - 1] = *reinterpret_cast<const float4 *>(pl + k * HX);
-    }
-    const float4 old = *reinterpret_cast<const float4 *>(sO + tz * TX + 4 * tx);
-    const float4 wv = *reinterpret_cast<const float4 *>(sW + tz * TX + 4 * tx);
-    const float xa[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
-    float pn[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float s[4];
-#pragma unroll
-        for (int k = 1; k <= 4; ++k)
-            s[k - 1] = (xa[4 + e + k] + xa[4 + e - k]) + (f4c(zp[k - 1], e) + f4c(zm[k - 1], e));
-        pn[e] = update_point<2>(prm, xa[4 + e], f4c(old, e), f4c(wv, e), axv[e] + azv, s[0], s[1], s[2],
-                                s[3]);
-    }
-    if (prm.src_on && z == prm.sz && (unsigned)(prm.sx - x) < 4u) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (prm.sx - x == e)
-                pn[e] += prm.src_amp;
-    }
-    if (z < prm.nz && x < prm.nx) {
-        float *dst = prm.out + (size_t)z * prm.px + x;
-        if (x + 3 < prm.nx) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (x + e < prm.nx)
-                    dst[e] = pn[e];
-        }
-    }
+    float2 r[2];
+    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r);
+    if (prm.src_on && z == prm.sz && (unsigned)(prm.sx - x) < 4u)
+        add_source4(r, prm.sx - x, prm.src_amp);
+    if (z < prm.nz && x < prm.nx)
+        store4(prm.out + (size_t)z * prm.px + x, r, prm.nx - x);
 }
 
 // ------------------------------------------------------------------------ helpers

@@ -82,6 +82,16 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
     asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
 
+// Bulk copy of `bytes` contiguous bytes from global to shared memory, completing
+// on bar.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // TMA tile load of a 2D box at element coordinates (x, y) into shared memory;
 // completion is signalled on bar as transaction bytes.  x * 4 bytes must be a
 // multiple of 16 (x % 4 == 0 for FP32); out-of-range elements read as zero.

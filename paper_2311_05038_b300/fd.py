@@ -37,6 +37,8 @@ EXPORTS = [
     "fd_reset", "fd_set_wavefield", "fd_step", "fd_run_shot", "fd_gather_traces", "fd_get_wavefield",
     "fd_synchronize", "fd_get_step", "fd_get_source_index", "fd_get_receiver_indices",
     "fd_get_damping_profile", "fd_kernel_launch_count", "fd_last_error",
+    "fd_batch_create", "fd_batch_destroy", "fd_batch_set_tuning", "fd_batch_get_tuning", "fd_batch_step",
+    "fd_batch_autotune",
 ]
 
 
@@ -52,6 +54,14 @@ class fd_grid_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double), ("dt", ctypes.c_double), ("sponge_width", ctypes.c_int),
                 ("sponge_R", ctypes.c_double)]
+
+
+class fd_batch_tuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("steps_per_launch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("group_mb", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _vp = ctypes.c_void_p
@@ -84,6 +94,12 @@ _SIGS = {
     "fd_get_receiver_indices": (_i, [_vp, _vp, _i]),
     "fd_get_damping_profile": (_i, [_vp, _i, _vp, _i]),
     "fd_kernel_launch_count": (ctypes.c_uint64, []),
+    "fd_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "fd_batch_destroy": (_i, [_vp]),
+    "fd_batch_set_tuning": (_i, [_vp, ctypes.POINTER(fd_batch_tuning)]),
+    "fd_batch_get_tuning": (_i, [_vp, ctypes.POINTER(fd_batch_tuning)]),
+    "fd_batch_step": (_i, [_vp, _i, _ip]),
+    "fd_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(fd_batch_tuning)]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -265,6 +281,42 @@ def fd_last_error() -> str:
     return _lib.fd_last_error().decode()
 
 
+def fd_batch_create(model_handles) -> int:
+    arr = (_vp * len(model_handles))(*model_handles)
+    out = _vp()
+    _check(_lib.fd_batch_create(arr, len(model_handles), ctypes.byref(out)), "fd_batch_create")
+    return out.value
+
+
+def fd_batch_destroy(b: int):
+    _check(_lib.fd_batch_destroy(b), "fd_batch_destroy")
+
+
+def fd_batch_set_tuning(b: int, tile: int, steps_per_launch: int, ctas_per_sm: int = 0, group_mb: int = 0):
+    t = fd_batch_tuning(int(tile), int(steps_per_launch), int(ctas_per_sm), int(group_mb))
+    _check(_lib.fd_batch_set_tuning(b, ctypes.byref(t)), "fd_batch_set_tuning")
+
+
+def fd_batch_get_tuning(b: int) -> dict:
+    t = fd_batch_tuning()
+    _check(_lib.fd_batch_get_tuning(b, ctypes.byref(t)), "fd_batch_get_tuning")
+    return t.as_dict()
+
+
+def fd_batch_step(b: int, nsteps: int, nsteps_each=None):
+    arr = None
+    if nsteps_each is not None:
+        each = np.ascontiguousarray(nsteps_each, dtype=np.int32)
+        arr = each.ctypes.data_as(_ip)
+    _check(_lib.fd_batch_step(b, int(nsteps), arr), "fd_batch_step")
+
+
+def fd_batch_autotune(b: int, trial_steps: int) -> dict:
+    t = fd_batch_tuning()
+    _check(_lib.fd_batch_autotune(b, int(trial_steps), ctypes.byref(t)), "fd_batch_autotune")
+    return t.as_dict()
+
+
 # ------------------------------------------------------------------ convenience
 
 class Model:
@@ -316,6 +368,50 @@ class Model:
     def close(self):
         if self.handle:
             fd_model_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning handle of one fd_batch over existing Model objects (kept alive here)."""
+
+    def __init__(self, models):
+        self.models = list(models)
+        self.handle = fd_batch_create([m.handle for m in self.models])
+
+    def set_tuning(self, tile=0, steps_per_launch=2000, ctas_per_sm=0, group_mb=96):
+        fd_batch_set_tuning(self.handle, tile, steps_per_launch, ctas_per_sm, group_mb)
+
+    def tuning(self):
+        return fd_batch_get_tuning(self.handle)
+
+    def step(self, nsteps, nsteps_each=None):
+        fd_batch_step(self.handle, nsteps, nsteps_each)
+
+    def run_shots(self, nts):
+        """Reset every shot, give shot i a library-owned trace buffer of nts[i] rows, run."""
+        for m, nt in zip(self.models, nts):
+            fd_reset(m.handle)
+            fd_set_trace_buffer(m.handle, None, int(nt))
+        fd_batch_step(self.handle, 0, np.asarray(nts, np.int32))
+
+    def autotune(self, trial_steps=20):
+        return fd_batch_autotune(self.handle, trial_steps)
+
+    def close(self):
+        if self.handle:
+            fd_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -1,0 +1,124 @@
+"""Batched multi-shot launches: every shot is bitwise the same alone and in a batch.
+
+The batch advances uneven 2D shots in one persistent launch (a table of
+(shot, tile) items gated by per-tile step counters).  Its arithmetic is the
+single-shot step's, so wavefields and traces must match fd_run_shot exactly
+under every tile shape, group budget and steps-per-launch setting, and for
+shots that stop at different steps.
+"""
+import numpy as np
+import pytest
+
+import pinlib as pl
+import workloads as wl
+from conftest import cuda_available
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+
+def small_shots(n=5, nt=120, seed=50):
+    rng = np.random.default_rng(seed)
+    shots = []
+    for i in range(n):
+        nz = int(rng.integers(40, 140))
+        nx = int(rng.integers(50, 220))
+        vel = wl.grf_velocity((nz, nx), corr_cells=5.0, vmin=1500.0, vmax=4000.0, seed=60 + i)
+        dt = wl.courant_dt(10.0, float(vel.max()))
+        rec = np.array([(ix, 0, min(12, nz - 1)) for ix in range(0, nx, 3)], np.int32)
+        shots.append(wl.Shot(2, (nz, nx), 10.0, dt, nt, vel, (nx // 2, 0, nz // 2), wl.ricker(nt, dt, 25.0),
+                             rec, sponge_width=8 if i % 2 == 0 else 0, name=f"batch-small-{i}"))
+    return shots
+
+
+def solo(fd, shots, nts):
+    out = []
+    for s, nt in zip(shots, nts):
+        with fd.Model.from_shot(s) as m:
+            m.run_shot(nt)
+            out.append((m.wavefield(with_old=True), m.traces(nt)))
+    return out
+
+
+def batched(fd, shots, nts, tuning):
+    models = [fd.Model.from_shot(s) for s in shots]
+    with fd.Batch(models) as b:
+        if tuning is not None:
+            b.set_tuning(**tuning)
+        b.run_shots(nts)
+        out = [(m.wavefield(with_old=True), m.traces(nt)) for m, nt in zip(models, nts)]
+    for m in models:
+        m.close()
+    return out
+
+
+def assert_same(a, b):
+    for (wa, ta), (wb, tb) in zip(a, b):
+        np.testing.assert_array_equal(wa[0], wb[0])
+        np.testing.assert_array_equal(wa[1], wb[1])
+        np.testing.assert_array_equal(ta, tb)
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(tile=0, steps_per_launch=2000, ctas_per_sm=0, group_mb=0),
+    dict(tile=1, steps_per_launch=37, ctas_per_sm=0, group_mb=0),
+    dict(tile=2, steps_per_launch=50, ctas_per_sm=1, group_mb=1),
+    dict(tile=0, steps_per_launch=7, ctas_per_sm=2, group_mb=1),
+])
+def test_batch_equals_solo_bitwise(fdlib, tuning):
+    shots = small_shots()
+    nts = [s.nt for s in shots]
+    assert_same(batched(fdlib, shots, nts, tuning), solo(fdlib, shots, nts))
+
+
+def test_batch_uneven_step_counts(fdlib):
+    shots = small_shots(n=4, nt=90, seed=51)
+    nts = [90, 17, 0, 64]
+    ref = solo(fdlib, shots, nts)
+    got = batched(fdlib, shots, nts, dict(tile=0, steps_per_launch=25, ctas_per_sm=0, group_mb=0))
+    assert_same(got, ref)
+
+
+def test_batch_matches_oracle(fdlib, oracle):
+    shots = small_shots(n=3, nt=150, seed=52)
+    got = batched(fdlib, shots, [s.nt for s in shots], None)
+    for s, ((P, Pold), tr) in zip(shots, got):
+        Pr, Poldr, trr = oracle.run(2, s.shape, s.h, s.dt, s.vel, sponge_width=s.sponge_width, src=s.src,
+                                    wavelet=s.wavelet, receivers=s.receivers, nsteps=s.nt)
+        assert pl.rel_l2(P, Pr) <= 1e-4 and pl.rel_l2(Pold, Poldr) <= 1e-4 and pl.rel_l2(tr, trr) <= 1e-4
+
+
+def test_batch_step_continues_a_run(fdlib):
+    """Two batch calls of 30 + 45 steps equal one solo run of 75."""
+    shots = small_shots(n=3, nt=75, seed=53)
+    ref = solo(fdlib, shots, [75, 75, 75])
+    models = [fdlib.Model.from_shot(s) for s in shots]
+    with fdlib.Batch(models) as b:
+        b.set_tuning(tile=1, steps_per_launch=16, ctas_per_sm=0, group_mb=0)
+        for m in models:
+            fdlib.fd_reset(m.handle)
+            fdlib.fd_set_trace_buffer(m.handle, None, 75)
+        b.step(30)
+        b.step(45)
+        got = [(m.wavefield(with_old=True), m.traces(75)) for m in models]
+        assert all(fdlib.fd_get_step(m.handle) == 75 for m in models)
+    assert_same(got, ref)
+
+
+def test_autotune_picks_a_valid_tuning(fdlib):
+    shots = small_shots(n=4, nt=60, seed=54)
+    models = [fdlib.Model.from_shot(s) for s in shots]
+    with fdlib.Batch(models) as b:
+        best = b.autotune(trial_steps=10)
+        assert best["tile"] in (0, 1, 2) and best["steps_per_launch"] == 2000
+        assert b.tuning() == best
+        b.run_shots([60] * 4)
+        got = [(m.wavefield(with_old=True), m.traces(60)) for m in models]
+    assert_same(got, solo(fdlib, shots, [60] * 4))
+
+
+def test_batch_rejects_3d_models(fdlib):
+    shot = wl.roofline_3d(shape=(16, 16, 16), nt=4, sponge_width=0)
+    with fdlib.Model.from_shot(shot) as m:
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_batch_create([m.handle])
+        assert e.value.status == fdlib.FD_EINVAL
