@@ -204,6 +204,31 @@ fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each);
  * trial steps change the models' state: call fd_reset or fd_run_shot after. */
 fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best);
 
+/* Allocation-free form of fd_batch_step.  The paper has no counterpart: it is
+ * an entry point for callers that cannot allocate device memory once they are
+ * running, such as a serving process whose memory pool already holds all the
+ * device memory it was given, or a latency-bound loop that must not pay the
+ * device-wide synchronisation that cudaMalloc and cudaFree imply.  Such a
+ * caller creates its 2D models at start-up (fd_model_create and friends) and
+ * advances them here: every model moves nsteps steps exactly as fd_step would,
+ * traces included, in one persistent launch on the first model's stream; the
+ * call returns when the work is done.
+ *
+ * No device or host memory is allocated.  The launch's scratch (shot
+ * descriptors, tile table, receiver lists, per-tile step counters, launch
+ * state, error word) lives in one static device array of about 1.8 MB that
+ * every device loading the library holds until the process exits.  Limits:
+ * at most 64 models, 32768 tiles of 64 x 16 points in total and 32768
+ * receivers in total; larger requests return FD_EBUDGET and change nothing.
+ * The first call on a device looks up the array's device address and sets the
+ * kernel's shared-memory limit, so make that first call before any stream
+ * capture.  Every call shares the array and leaves its tables there; the call
+ * clears the counters, launch state and error word it uses before launching.
+ * Calls that overlap on the GPU (from several host threads, or processes
+ * sharing a context) race on the array and must be serialised by the caller.
+ * Errors as fd_batch_step (FD_EINVAL, FD_EBUDGET, FD_ECUDA, FD_ETIMEOUT). */
+fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels, int nsteps);
+
 /* Number of CUDA kernel launches this library has issued since load. */
 uint64_t fd_kernel_launch_count(void);
 

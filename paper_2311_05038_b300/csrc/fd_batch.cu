@@ -754,3 +754,209 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
         *best = best_t;
     return fd_batch_set_tuning(b, &best_t);
 }
+
+// ------------------------------------------------------------ allocation-free variant
+//
+// fd_batch_step_noalloc runs the same persistent kernel as fd_batch_step over
+// caller-created models, but takes every piece of scratch it needs (shot
+// descriptors with their tensor maps, the tile table, the per-tile receiver
+// lists, the per-tile step counters, the launch state and the error word) from
+// one file-scope device array instead of device allocations.  Host-side it
+// stages the tables in a file-scope host buffer of the same layout, so it
+// makes no heap allocation either.
+
+namespace {
+
+constexpr int kNoAllocMaxShots = 64;
+constexpr int kNoAllocMaxItems = 32768;   // 64 x 16 tiles in total over all shots
+constexpr int kNoAllocMaxRecs = 32768;    // receivers in total over all shots
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocScratch {
+    ShotDesc shots[kNoAllocMaxShots];
+    BatchItem items[kNoAllocMaxItems];
+    BatchRec recs[kNoAllocMaxRecs];
+    int counters[kNoAllocMaxItems];
+    int group_begin[2];
+    BatchState state;
+    int err;
+};
+
+NoAllocScratch h_noalloc;                           // host staging of the tables
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};      // device address of the array, per device
+bool g_noalloc_ready[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+// The scratch itself: shared by every call on a device, kept between calls.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+extern "C" fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels, int nsteps)
+{
+    if (!models || nmodels < 1 || nsteps < 0)
+        return fail(FD_EINVAL, "fd_batch_step_noalloc: bad arguments");
+    if (nmodels > kNoAllocMaxShots)
+        return fail(FD_EBUDGET, "fd_batch_step_noalloc: %d shots exceed the static limit of %d", nmodels,
+                    kNoAllocMaxShots);
+    for (int i = 0; i < nmodels; ++i) {
+        if (!models[i] || models[i]->d.ndim != 2)
+            return fail(FD_EINVAL, "fd_batch_step_noalloc: model %d is NULL or not 2D", i);
+        if (models[i]->device != models[0]->device)
+            return fail(FD_EINVAL, "fd_batch_step_noalloc: models on different devices");
+        for (int j = 0; j < i; ++j)
+            if (models[j] == models[i])
+                return fail(FD_EINVAL, "fd_batch_step_noalloc: model %d repeated", i);
+    }
+    const Variant v = get_variant(0);
+    long long nitems = 0, nrecs = 0;
+    for (int i = 0; i < nmodels; ++i) {
+        const fd_model *m = models[i];
+        nitems += (long long)((m->nx + v.tx - 1) / v.tx) * ((m->nz + v.tz - 1) / v.tz);
+        nrecs += m->nrec;
+    }
+    if (nitems > kNoAllocMaxItems)
+        return fail(FD_EBUDGET, "fd_batch_step_noalloc: %lld tiles of %dx%d exceed the static limit of %d", nitems,
+                    v.tx, v.tz, kNoAllocMaxItems);
+    if (nrecs > kNoAllocMaxRecs)
+        return fail(FD_EBUDGET, "fd_batch_step_noalloc: %lld receivers exceed the static limit of %d", nrecs,
+                    kNoAllocMaxRecs);
+    const int dev = models[0]->device;
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(FD_EINVAL, "fd_batch_step_noalloc: device %d out of range", dev);
+    FD_CUDA(cudaSetDevice(dev), "cudaSetDevice");
+
+    // One-time set-up on this device (the device is current): the device
+    // address of the array, and the kernel's shared-memory limit.
+    if (!g_noalloc_ready[dev]) {
+        FD_CUDA(cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch), "scratch address");
+        FD_CUDA(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem),
+                "kernel attributes");
+        g_noalloc_ready[dev] = true;
+    }
+    unsigned char *dbase = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    NoAllocScratch &h = h_noalloc;
+
+    // tables: one group holding every shot, 64 x 16 tiles
+    int ni = 0, nr = 0;
+    for (int s = 0; s < nmodels; ++s) {
+        fd_model *m = models[s];
+        ShotDesc &d = h.shots[s];
+        d = ShotDesc{};
+        bool ok = true;
+        for (int i = 0; i < 2; ++i) {
+            ok = ok && make_map(&d.halo[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, v.tx + 8, v.tz + 8);
+            ok = ok && make_map(&d.tile[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, v.tx, v.tz);
+            d.buf[i] = m->buf[i];
+        }
+        ok = ok && make_map(&d.wmap, m->w, 2, m->nx, 1, m->nz, m->px, v.tx, v.tz);
+        if (!ok)
+            return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed for shot %d", s);
+        d.ax = m->ax;
+        d.az = m->az;
+        d.amp = m->d_amp;
+        d.namp = m->src_on ? (int)m->amp.size() : 0;
+        d.src_on = m->src_on;
+        d.sx = m->sx;
+        d.sz = m->sz;
+        d.traces = m->nrec > 0 ? m->traces : nullptr;
+        d.trace_rows = d.traces ? m->trace_rows : 0;
+        d.nrec = m->nrec;
+        d.nx = m->nx;
+        d.nz = m->nz;
+        d.px = m->px;
+        d.n0 = m->n;
+        d.cur0 = m->cur;
+        d.target = nsteps;
+        d.has_sponge = m->has_sponge;
+        const int tx_n = (m->nx + v.tx - 1) / v.tx, tz_n = (m->nz + v.tz - 1) / v.tz;
+        const int base = ni;
+        for (int t = 0; t < tx_n * tz_n; ++t) {
+            BatchItem &it = h.items[base + t];
+            const int tx = t % tx_n, tz = t / tx_n;
+            it.shot = s;
+            it.x0 = tx * v.tx;
+            it.z0 = tz * v.tz;
+            it.nb[0] = tx > 0 ? base + t - 1 : -1;
+            it.nb[1] = tx + 1 < tx_n ? base + t + 1 : -1;
+            it.nb[2] = tz > 0 ? base + t - tx_n : -1;
+            it.nb[3] = tz + 1 < tz_n ? base + t + tx_n : -1;
+            it.rec_begin = nr;
+            // receivers of this tile, in receiver order
+            for (int r = 0; r < m->nrec; ++r) {
+                const int64_t di = m->rec_dense[r];
+                const int ix = (int)(di % m->nx), iz = (int)(di / m->nx);
+                if (ix / v.tx == tx && iz / v.tz == tz)
+                    h.recs[nr++] = BatchRec{(iz % v.tz) * v.tx + ix % v.tx, r};
+            }
+            it.rec_end = nr;
+        }
+        ni += tx_n * tz_n;
+    }
+    h.group_begin[0] = 0;
+    h.group_begin[1] = ni;
+
+    for (int s = 0; s < nmodels; ++s)
+        FD_CUDA(cudaStreamSynchronize(models[s]->stream), "model stream");
+    cudaStream_t st = models[0]->stream;
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dbase + off, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    FD_CUDA(up(offsetof(NoAllocScratch, shots), h.shots, nmodels * sizeof(ShotDesc)), "scratch upload");
+    FD_CUDA(up(offsetof(NoAllocScratch, items), h.items, ni * sizeof(BatchItem)), "scratch upload");
+    FD_CUDA(up(offsetof(NoAllocScratch, recs), h.recs, nr * sizeof(BatchRec)), "scratch upload");
+    FD_CUDA(up(offsetof(NoAllocScratch, group_begin), h.group_begin, sizeof h.group_begin), "scratch upload");
+    // what must start at zero: the counters in use, the launch state and the error word
+    FD_CUDA(cudaMemsetAsync(dbase + offsetof(NoAllocScratch, counters), 0, ni * sizeof(int), st), "scratch clear");
+    FD_CUDA(cudaMemsetAsync(dbase + offsetof(NoAllocScratch, state), 0, sizeof(BatchState), st), "scratch clear");
+    FD_CUDA(cudaMemsetAsync(dbase + offsetof(NoAllocScratch, err), 0, sizeof(int), st), "scratch clear");
+
+    if (nsteps > 0 && ni > 0) {
+        float w4[4];
+        fd_stencil_weights(w4);
+        BatchParams p{};
+        p.shots = reinterpret_cast<const ShotDesc *>(dbase + offsetof(NoAllocScratch, shots));
+        p.items = reinterpret_cast<const BatchItem *>(dbase + offsetof(NoAllocScratch, items));
+        p.recs = reinterpret_cast<const BatchRec *>(dbase + offsetof(NoAllocScratch, recs));
+        p.counters = reinterpret_cast<int *>(dbase + offsetof(NoAllocScratch, counters));
+        p.group_begin = reinterpret_cast<const int *>(dbase + offsetof(NoAllocScratch, group_begin));
+        p.ngroups = 1;
+        p.K = nsteps;
+        p.state = reinterpret_cast<BatchState *>(dbase + offsetof(NoAllocScratch, state));
+        p.c1 = w4[0];
+        p.c2 = w4[1];
+        p.c3 = w4[2];
+        p.c4 = w4[3];
+        p.err = reinterpret_cast<int *>(dbase + offsetof(NoAllocScratch, err));
+        int per_sm = 0, sms = 0;
+        FD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.threads, v.smem), "occupancy");
+        FD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+        if (per_sm < 1)
+            return fail(FD_ECUDA, "batch kernel does not fit on an SM");
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(sms * per_sm);
+        cfg.blockDim = dim3(v.threads);
+        cfg.dynamicSmemBytes = v.smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {(void *)&p};
+        FD_CUDA(cudaLaunchKernelExC(&cfg, v.fn, args), "batch kernel launch");
+        ++g_launches;
+    }
+    FD_CUDA(cudaStreamSynchronize(st), "batch run");
+    int err = 0;
+    FD_CUDA(cudaMemcpy(&err, dbase + offsetof(NoAllocScratch, err), sizeof err, cudaMemcpyDeviceToHost),
+            "error word");
+    for (int s = 0; s < nmodels; ++s) {
+        fd_model *m = models[s];
+        m->n += nsteps;
+        m->cur ^= nsteps & 1;
+        m->pending_row = -1;
+    }
+    if (err)
+        return fail(FD_ETIMEOUT, "a batch dependency wait gave up (device code %d)", err);
+    return FD_OK;
+}
