@@ -41,7 +41,7 @@ BYTES_PER_UPDATE = 16          # read P, Pold, w; write Pn (FP32)
 FALLBACK_HBM_GBS = 6400.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fd_step3d_512cube_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2311_05038_b300", "csrc", f)
-                  for f in ("fd_kernels.cu", "fd_internal.h", "ptx.cuh")]
+                  for f in ("fd_kernels.cu", "fd_internal.h", "ptx.cuh", "stencil.cuh")]
 
 
 def parse_args():
@@ -55,6 +55,11 @@ def parse_args():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-unfused", action="store_true")
+    ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched"])
+    ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
+    ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
     return ap.parse_args()
 
 
@@ -227,6 +232,100 @@ def run_reference(args, dist, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------ batched 2D
+
+def measure_batched(nshots=64, nt=2000, repeats=1):
+    """The batched 2D workload served two ways on this GPU: one shot at a time
+    (fd_run_shot per shot, back to back) and all shots in one persistent batch
+    (autotuned).  Returns a summary dict; results are compared bitwise."""
+    import torch
+    from paper_2311_05038_b300 import fd
+    shapes = wl.batched_2d_shapes(nshots)
+    shots = [wl.batched_2d_shot(i, s, nt) for i, s in enumerate(shapes)]
+    updates = sum(s.npoints for s in shots) * nt
+    models = [fd.Model.from_shot(s) for s in shots]
+
+    def plain():
+        for m in models:
+            m.run_shot(nt)
+        for m in models:
+            fd.fd_synchronize(m.handle)
+
+    def timed(fn):
+        fn()                                  # warm-up pass
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(repeats):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / repeats
+
+    launches0 = fd.fd_kernel_launch_count()
+    t_plain = timed(plain)
+    plain_launches = (fd.fd_kernel_launch_count() - launches0) // (repeats + 1)
+    ref = [m.traces(nt).copy() for m in models]
+    ref_p = [m.wavefield() for m in models[:8]]
+    batch = fd.Batch(models)
+    tuning = batch.autotune(trial_steps=20)
+    launches0 = fd.fd_kernel_launch_count()
+    t_batch = timed(lambda: batch.run_shots([nt] * nshots))
+    batch_launches = (fd.fd_kernel_launch_count() - launches0) // (repeats + 1)
+    same = all(np.array_equal(m.traces(nt), r) for m, r in zip(models, ref)) and \
+        all(np.array_equal(m.wavefield(), p) for m, p in zip(models[:8], ref_p))
+    batch.close()
+    for m in models:
+        m.close()
+    return {
+        "workload": f"{nshots} 2D shots {min(shapes)}..{max(shapes)} (nz, nx), GRF velocity, sponge 20, {nt} steps",
+        "updates": updates,
+        "plain": {"s": t_plain, "shots_per_s": nshots / t_plain, "gupd": updates / t_plain / 1e9,
+                  "launches": int(plain_launches)},
+        "batched": {"s": t_batch, "shots_per_s": nshots / t_batch, "gupd": updates / t_batch / 1e9,
+                    "launches": int(batch_launches), "tuning": tuning},
+        "speedup": t_plain / t_batch,
+        "results_identical": bool(same),
+    }
+
+
+# ------------------------------------------------------------------------ unfused 3D
+
+def measure_unfused(shot, model, stream, reps=20):
+    """Per-routine times of the paper's unfused sequence on the benchmark grid,
+    each against its own algorithmic bytes, and the whole unfused step."""
+    import torch
+    from paper_2311_05038_b300 import fd
+    npts = shot.npoints
+    routines = [("fd_pzz", fd.FD_ROUTINE_PZZ, 8), ("fd_pxx", fd.FD_ROUTINE_PXX, 8), ("fd_pyy", fd.FD_ROUTINE_PYY, 8),
+                ("fd_time", fd.FD_ROUTINE_TIME, 28)]
+    peak, _ = measured_hbm_peak()
+    out = {}
+    for name, r, bpp in routines:
+        fd.fd_routine(model.handle, r)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fd.fd_routine(model.handle, r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        out[name] = {"us": t * 1e6, "bytes_per_update": bpp, "GBs": bpp * npts / t / 1e9,
+                     "frac": bpp * npts / t / 1e9 / peak}
+    fd.fd_reset(model.handle)
+    fd.fd_step_unfused(model.handle, 2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fd.fd_step_unfused(model.handle, reps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    return {"routines": out, "step_us": t * 1e6, "gupd": npts / t / 1e9, "bytes_per_update": 52,
+            "note": "the paper's add_source, fd_pzz, fd_pxx, fd_pyy, fd_time, swap as separate kernels"}
+
+
 # ------------------------------------------------------------------------ main arm
 
 def run_b300(args, dist, rank, local, world):
@@ -279,6 +378,10 @@ def run_b300(args, dist, rank, local, world):
     achieved = BYTES_PER_UPDATE * npts / avg_launch_s / 1e9
     peak, peak_kind = measured_hbm_peak()
 
+    unfused = None
+    if rank == 0 and not args.skip_unfused:
+        unfused = measure_unfused(shot, model, stream)
+
     # ---- end to end: velocity up from pinned host memory, traces back, every step
     e2e = None
     if not args.skip_e2e:
@@ -316,6 +419,11 @@ def run_b300(args, dist, rank, local, world):
                "sample": f"{args.n}^3 layered grid with sponge, source and receivers, {steps} of "
                          f"{args.nt} time steps, FP64 oracle, {el:.1f} s"}
 
+    batched = None
+    if rank == 0 and not args.skip_batched:
+        torch.cuda.empty_cache()
+        batched = measure_batched(args.shots, args.batch_nt)
+
     if rank == 0:
         traffic = recorded_traffic(args.n)
         line = {
@@ -336,8 +444,23 @@ def run_b300(args, dist, rank, local, world):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "gpu_launches": int(launches),
+            "batched_2d": batched,
+            "unfused_3d": unfused,
         }
         print(json.dumps(line), flush=True)
+
+
+def run_batched_line(args, rank):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return
+    r = measure_batched(args.shots, args.batch_nt, repeats=max(1, args.steps))
+    line = {"metric": "shots/s (batched 2D)", "value": r["batched"]["shots_per_s"], "unit": "shots/s",
+            "n_gpus": 1, "steps": max(1, args.steps), "warmup": 1, "ms_per_step": r["batched"]["s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -346,6 +469,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist, rank, world)
+        elif args.workload == "batched":
+            run_batched_line(args, rank)
         else:
             run_b300(args, dist, rank, local, world)
     finally:

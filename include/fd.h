@@ -159,6 +159,29 @@ fd_status fd_get_source_index(fd_model *m, int64_t *idx);
 fd_status fd_get_receiver_indices(fd_model *m, int64_t *out, int cap);
 fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
 
+/* --------------------------------------------------------- unfused routines
+ *
+ * The paper's routines one kernel each, as in its WaveSimulator::run()
+ * (section 7, Listing 3): fd_pzz, fd_pxx (and, in 3D, the y counterpart) each
+ * write one second-derivative field D2 = sum_k c_k ((P[+k] + P[-k]) - 2P);
+ * fd_time writes Pn = (2P - (1 - a) Pold + w (Pxx [+ Pyy] + Pzz)) / (1 + a) over
+ * Pold; add_source adds dt^2 S(t_n) / h^d to Pn; the swap gathers the step's
+ * receivers and rotates the levels (step counter + 1).  The derivative fields
+ * are allocated on first use.  This schedule moves ~40 B per update in 2D
+ * (52 in 3D) against fd_step's 16 and exists for comparison on the same
+ * hardware; it computes the same recurrence up to the order in which the axes
+ * are summed.  Calls are asynchronous on the model's stream. */
+#define FD_ROUTINE_ADD_SOURCE 0
+#define FD_ROUTINE_PZZ        1
+#define FD_ROUTINE_PXX        2
+#define FD_ROUTINE_PYY        3
+#define FD_ROUTINE_TIME       4
+#define FD_ROUTINE_SWAP       5
+/* One routine (FD_EINVAL for an unknown one, or PYY on a 2D model). */
+fd_status fd_routine(fd_model *m, int routine);
+/* nsteps steps of the sequence PZZ, PXX, [PYY,] TIME, ADD_SOURCE, SWAP. */
+fd_status fd_step_unfused(fd_model *m, int nsteps);
+
 /* ----------------------------------------------------------------- batches
  *
  * A batch advances many independent 2D shots (models) in one persistent,

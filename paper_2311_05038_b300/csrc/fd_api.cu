@@ -203,6 +203,8 @@ static void free_model(fd_model *m)
     cudaFree(m->d_rec);
     cudaFree(m->d_amp);
     cudaFree(m->stage);
+    for (float *d : m->deriv)
+        cudaFree(d);
     if (m->traces_owned)
         cudaFree(m->traces);
     delete m;

@@ -56,4 +56,6 @@ struct fd_model {
 
     int n = 0;
     int pending_row = -1;      // receiver row whose gather is still owed
+
+    float *deriv[3] = {nullptr, nullptr, nullptr};   // Pxx, Pyy, Pzz of the unfused routines
 };

@@ -38,7 +38,7 @@ EXPORTS = [
     "fd_synchronize", "fd_get_step", "fd_get_source_index", "fd_get_receiver_indices",
     "fd_get_damping_profile", "fd_kernel_launch_count", "fd_last_error",
     "fd_batch_create", "fd_batch_destroy", "fd_batch_set_tuning", "fd_batch_get_tuning", "fd_batch_step",
-    "fd_batch_autotune", "fd_batch_step_noalloc",
+    "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
 ]
 
 
@@ -101,6 +101,8 @@ _SIGS = {
     "fd_batch_step": (_i, [_vp, _i, _ip]),
     "fd_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(fd_batch_tuning)]),
     "fd_batch_step_noalloc": (_i, [ctypes.POINTER(_vp), _i, _i]),
+    "fd_routine": (_i, [_vp, _i]),
+    "fd_step_unfused": (_i, [_vp, _i]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -322,6 +324,17 @@ def fd_batch_step_noalloc(model_handles, nsteps: int):
     """Advance the given 2D models nsteps steps without allocating device memory."""
     arr = (_vp * len(model_handles))(*model_handles)
     _check(_lib.fd_batch_step_noalloc(arr, len(model_handles), int(nsteps)), "fd_batch_step_noalloc")
+
+
+FD_ROUTINE_ADD_SOURCE, FD_ROUTINE_PZZ, FD_ROUTINE_PXX, FD_ROUTINE_PYY, FD_ROUTINE_TIME, FD_ROUTINE_SWAP = range(6)
+
+
+def fd_routine(m: int, routine: int):
+    _check(_lib.fd_routine(m, int(routine)), "fd_routine")
+
+
+def fd_step_unfused(m: int, nsteps: int):
+    _check(_lib.fd_step_unfused(m, int(nsteps)), "fd_step_unfused")
 
 
 # ------------------------------------------------------------------ convenience
