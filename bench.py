@@ -57,7 +57,9 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-unfused", action="store_true")
-    ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched"])
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-shots", type=int, default=48, help="serving workload: requests in the stream")
+    ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
     ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
     return ap.parse_args()
@@ -287,6 +289,62 @@ def measure_batched(nshots=64, nt=2000, repeats=1):
     }
 
 
+# ------------------------------------------------------------------------ serving 3D
+
+def measure_serving(nshots=48, max_active=8, load=0.8, budget_gb=150):
+    """The serving workload: a Poisson stream of 3D shots (cubes 128..384, 200..2000
+    steps) served by continuous batching and one at a time.  Open loop: arrivals
+    at `load` times the one-at-a-time service rate (calibrated here), reporting
+    p50/p99 latency.  Closed loop: every request queued at t = 0, reporting
+    shots/s.  Traces are compared bitwise between the modes."""
+    import torch
+    from paper_2311_05038_b300 import fd, serving
+    sizes = list(range(128, 385, 32))
+    cache = {}
+    for n in sizes:
+        for k in range(2):
+            cache[(n, k)] = torch.from_numpy(wl.serving_3d_velocity(n, 4000 + 10 * n + k)).pin_memory()
+    per_step = {}
+    for n in sizes:
+        shot = wl.serving_3d_shot(0, n, 100, vel=cache[(n, 0)].numpy())
+        with fd.Model.from_shot(shot) as m:
+            m.run_shot(20)
+            fd.fd_synchronize(m.handle)
+            t0 = time.perf_counter()
+            m.run_shot(100)
+            fd.fd_synchronize(m.handle)
+            per_step[n] = (time.perf_counter() - t0) / 100
+    base = wl.serving_3d_stream(nshots, seed=4, rate=1.0)
+    mean_service = float(np.mean([nt * per_step[n] for _, n, nt in base]))
+    rate = load / mean_service
+    stream = wl.serving_3d_stream(nshots, seed=4, rate=rate)
+    reqs = []
+    for i, (arr, n, nt) in enumerate(stream):
+        vel = cache[(n, i % 2)]
+        reqs.append(serving.Request(i, arr, wl.serving_3d_shot(i, n, nt, vel=vel.numpy()), vel))
+    out = {"workload": f"{nshots} 3D shots, cubes 128..384, 200..2000 steps, Poisson arrivals",
+           "rate_per_s": rate, "mean_service_s_one_at_a_time": mean_service, "budget_gb": budget_gb,
+           "max_active": max_active}
+    traces = {}
+    for mode, ma in (("continuous", max_active), ("one_at_a_time", 1)):
+        srv = serving.Server(max_active=ma, budget_bytes=int(budget_gb * 1e9), chunk=100, depth=2, max_nt=2000)
+        srv.serve(reqs[:4], realtime=False)                      # warm the pool
+        t0 = time.perf_counter()
+        res = srv.serve(reqs, realtime=True)
+        open_loop = serving.summarize(res, time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        res_c = srv.serve(reqs, realtime=False)
+        closed = serving.summarize(res_c, time.perf_counter() - t0)
+        out[mode] = {"open_loop": open_loop, "closed_loop": closed, "peak_hbm_gb": srv.pool.peak / 1e9}
+        traces[mode] = [r.traces for r in res]
+        srv.close()
+    out["results_identical"] = all(np.array_equal(a, b) for a, b in zip(traces["continuous"],
+                                                                       traces["one_at_a_time"]))
+    out["closed_loop_speedup"] = (out["continuous"]["closed_loop"]["shots_per_s"] /
+                                  out["one_at_a_time"]["closed_loop"]["shots_per_s"])
+    return out
+
+
 # ------------------------------------------------------------------------ unfused 3D
 
 def measure_unfused(shot, model, stream, reps=20):
@@ -423,6 +481,10 @@ def run_b300(args, dist, rank, local, world):
     if rank == 0 and not args.skip_batched:
         torch.cuda.empty_cache()
         batched = measure_batched(args.shots, args.batch_nt)
+    served = None
+    if rank == 0 and not args.skip_serving:
+        torch.cuda.empty_cache()
+        served = measure_serving(args.serve_shots)
 
     if rank == 0:
         traffic = recorded_traffic(args.n)
@@ -445,6 +507,7 @@ def run_b300(args, dist, rank, local, world):
             "clocks": clocks.summary(),
             "gpu_launches": int(launches),
             "batched_2d": batched,
+            "serving_3d": served,
             "unfused_3d": unfused,
         }
         print(json.dumps(line), flush=True)
@@ -463,6 +526,22 @@ def run_batched_line(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_line(args, rank):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return
+    nshots = args.serve_shots if args.serve_shots != 48 else 500
+    r = measure_serving(nshots)
+    c = r["continuous"]
+    line = {"metric": "shots/s (served 3D, continuous batching)", "value": c["closed_loop"]["shots_per_s"],
+            "unit": "shots/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": c["closed_loop"]["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": {"workload": r["workload"]},
+            "p50_s": c["open_loop"]["p50_s"], "p99_s": c["open_loop"]["p99_s"], "detail": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist, rank, local, world = dist_setup(args)
@@ -471,6 +550,8 @@ def main():
             run_reference(args, dist, rank, world)
         elif args.workload == "batched":
             run_batched_line(args, rank)
+        elif args.workload == "serving":
+            run_serving_line(args, rank)
         else:
             run_b300(args, dist, rank, local, world)
     finally:

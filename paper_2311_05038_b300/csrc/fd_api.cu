@@ -364,9 +364,13 @@ static fd_status create(const fd_grid_desc *desc, const float *v, cudaMemcpyKind
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
         const long long tiles = (long long)((m->nx + kTX3 - 1) / kTX3) * ((m->ny + kTY3 - 1) / kTY3);
         const long long slots = (long long)sms * step3d_blocks_per_sm();
-        // About six waves of CTAs, each marching at least 32 planes.
+        // About six waves of CTAs, each marching at least 32 planes; grids whose
+        // three fields fit in L2 may use chunks down to 8 planes (the extra halo
+        // planes are re-read from L2), so that small shots still fill the GPU.
+        const bool l2_resident = 3.0 * m->pitched * sizeof(float) <= 96.0 * 1048576.0;
+        const long long bz_min = l2_resident ? 8 : 32;
         long long bz = (long long)m->nz * tiles / (6 * slots);
-        bz = std::max(32LL, std::min<long long>(bz, m->nz));
+        bz = std::max(bz_min, std::min<long long>(bz, m->nz));
         m->nchunks = (int)((m->nz + bz - 1) / bz);
         m->bz = (m->nz + m->nchunks - 1) / m->nchunks;
     }

@@ -22,7 +22,9 @@ benchmark configurations, every random draw seeded):
   {512, ..., 1024}; velocity = white noise (seed 3 + shot) smoothed by a
   Gaussian of 20 cells (200 m) and mapped affinely onto [1500, 4000]; 2000 steps.
 * ``serving_3d``: a Poisson stream of shots (seed 4) with cubes n in
-  {128, 160, ..., 384} and nt in [200, 2000].
+  {128, 160, ..., 384} and nt in [200, 2000]; velocity = the layered model plus
+  500 m/s times a product of three 1D Gaussian random fields (200 m), clipped
+  to [1500, 4500]; dt at Courant 0.4 of 4500 m/s.
 * ``adjoint_3d``: 256^3 smoothed random velocity in [1500, 4000] (seed 5).
 """
 from __future__ import annotations
@@ -198,18 +200,42 @@ def serving_3d_stream(nshots: int = 500, seed: int = 4, rate: float = 1.0,
     return [(float(a), int(n), int(t)) for a, n, t in zip(arrivals, ns, nts)]
 
 
-def serving_3d_shot(i: int, n: int, nt: int, seed: int = 4, sponge_width: int = 20) -> Shot:
-    """Shot i of the serving workload: layered + random velocity, clipped to [1500, 4500]."""
+def smooth_profile(n: int, corr_cells: float, seed: int) -> np.ndarray:
+    """1D white noise smoothed by a Gaussian of std corr_cells, scaled to max |.| = 1 (FP64)."""
+    g = random_field((n,), corr_cells, seed)
+    return g / max(np.abs(g).max(), 1e-300)
+
+
+def serving_3d_velocity(n: int, seed: int, sponge_width: int = 20) -> np.ndarray:
+    """Layered model (10 flat layers, U(1500, 4500)) plus a smooth random perturbation,
+    clipped to [1500, 4500] (FP32).  The perturbation is 500 m/s times the product of
+    three independent 1D Gaussian random fields of correlation length 200 m (20 cells),
+    which keeps generation O(n^3) elementwise for the large stream of serving shots."""
     shape = (n, n, n)
-    lay = layered_velocity(shape, seed=seed * 1000 + i).astype(np.float64)
-    g = random_field(shape, 20.0, seed * 1000 + i + 500000)
-    g = g / max(np.abs(g).max(), 1e-300) * 500.0
-    vel = np.clip(lay + g, 1500.0, 4500.0).astype(np.float32)
+    lay = layered_velocity(shape, seed=seed)
+    gz = smooth_profile(n, 20.0, seed + 11)[:, None, None]
+    gy = smooth_profile(n, 20.0, seed + 12)[None, :, None]
+    gx = smooth_profile(n, 20.0, seed + 13)[None, None, :]
+    v = lay.astype(np.float64) + 500.0 * gz * gy * gx
+    return np.clip(v, 1500.0, 4500.0).astype(np.float32)
+
+
+def serving_3d_shot(i: int, n: int, nt: int, seed: int = 4, sponge_width: int = 20, vel=None,
+                    src_jitter: bool = True) -> Shot:
+    """Shot i of the serving workload on an n^3 grid: 10 Hz source near the top (its
+    x, y position drawn per shot), receivers every 2nd point of plane iz = W + 5 over
+    the central half."""
+    shape = (n, n, n)
+    if vel is None:
+        vel = serving_3d_velocity(n, seed * 1000 + i, sponge_width)
     h, f = 10.0, 10.0
-    dt = courant_dt(h, float(vel.max()))
-    src = (n // 2, n // 2, sponge_width + 10)
+    dt = courant_dt(h, 4500.0)      # one dt for the stream: Courant 0.4 at the clip velocity
+    rng = np.random.default_rng(seed * 7919 + i)
+    cx = n // 2 + (int(rng.integers(-n // 8, n // 8 + 1)) if src_jitter else 0)
+    cy = n // 2 + (int(rng.integers(-n // 8, n // 8 + 1)) if src_jitter else 0)
+    src = (cx, cy, min(sponge_width + 10, n - 1))
     xs = range(n // 4, 3 * n // 4, 2)
-    rec = np.array([(ix, iy, sponge_width + 5) for iy in xs for ix in xs], dtype=np.int32)
+    rec = np.array([(ix, iy, min(sponge_width + 5, n - 1)) for iy in xs for ix in xs], dtype=np.int32)
     return Shot(ndim=3, shape=shape, h=h, dt=dt, nt=nt, vel=vel, src=src,
                 wavelet=ricker(nt, dt, f), receivers=rec, sponge_width=sponge_width,
                 name=f"3d-serve-{n}-{nt}-shot{i}")
