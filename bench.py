@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-unfused", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--adjoint-shots", type=int, default=2, help="adjoint workload: shots per gradient")
     ap.add_argument("--serve-shots", type=int, default=48, help="serving workload: requests in the stream")
     ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
@@ -345,6 +347,52 @@ def measure_serving(nshots=48, max_active=8, load=0.8, budget_gb=150):
     return out
 
 
+# ------------------------------------------------------------------------ adjoint 3D
+
+def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
+    """Gradient of the trace misfit w.r.t. squared slowness for the adjoint
+    workload (observed data from the +5 % anomaly model): time per gradient
+    over all shots, the forward share, and the device memory it held."""
+    import torch
+    from paper_2311_05038_b300 import adjoint, fd
+    shots, v_true = wl.adjoint_3d(n, nt, nshots)
+    vmax = 4000.0 * 1.05
+    observed = []
+    for s in shots:
+        s2 = wl.Shot(3, s.shape, s.h, s.dt, nt, v_true, s.src, s.wavelet, s.receivers, sponge_width=s.sponge_width)
+        with fd.Model.from_shot(s2) as m:
+            fd.fd_set_sponge_vmax(m.handle, vmax)
+            m.run_shot(nt)
+            observed.append(torch.from_numpy(m.traces(nt)).cuda())
+    m0 = torch.from_numpy((1.0 / shots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    t0 = time.perf_counter()
+    grad = torch.zeros_like(m0)
+    J = 0.0
+    for s, dobs in zip(shots, observed):
+        geo = adjoint.Geometry.from_shot(s, checkpoint_every=checkpoint_every, sponge_vmax=vmax)
+        Js, gs = adjoint.misfit_and_gradient(m0, geo, dobs)
+        J += Js
+        grad += gs
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    peak = torch.cuda.max_memory_allocated() - base
+    # forward-only time for the same shots, for the ratio
+    t0 = time.perf_counter()
+    for s in shots:
+        geo = adjoint.Geometry.from_shot(s, checkpoint_every=checkpoint_every, sponge_vmax=vmax)
+        with torch.no_grad():
+            adjoint.Propagate.apply(m0, geo)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    return {"workload": f"{nshots} shots, {n}^3, {nt} steps, checkpoints every {checkpoint_every}",
+            "s_per_gradient": el, "forward_s": fwd, "gradient_over_forward": el / fwd, "misfit": J,
+            "peak_torch_memory_gb": peak / 1e9, "gupd_forward_equivalent": nshots * nt * n ** 3 / el / 1e9,
+            "grad_norm": float(grad.norm())}
+
+
 # ------------------------------------------------------------------------ unfused 3D
 
 def measure_unfused(shot, model, stream, reps=20):
@@ -481,6 +529,10 @@ def run_b300(args, dist, rank, local, world):
     if rank == 0 and not args.skip_batched:
         torch.cuda.empty_cache()
         batched = measure_batched(args.shots, args.batch_nt)
+    adj = None
+    if rank == 0 and not args.skip_adjoint:
+        torch.cuda.empty_cache()
+        adj = measure_adjoint(nshots=args.adjoint_shots)
     served = None
     if rank == 0 and not args.skip_serving:
         torch.cuda.empty_cache()
@@ -508,6 +560,7 @@ def run_b300(args, dist, rank, local, world):
             "gpu_launches": int(launches),
             "batched_2d": batched,
             "serving_3d": served,
+            "adjoint_3d": adj,
             "unfused_3d": unfused,
         }
         print(json.dumps(line), flush=True)

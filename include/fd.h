@@ -109,6 +109,11 @@ fd_status fd_model_destroy(fd_model *m);
 fd_status fd_set_velocity(fd_model *m, const float *v_host);
 fd_status fd_set_velocity_dev(fd_model *m, const float *v_dev);
 
+/* Fix the sponge strength to that of velocity vmax (m/s) instead of the model's
+ * largest velocity, now and across later fd_set_velocity calls (0 restores the
+ * default).  Lets the damping stay fixed while an inversion changes the model. */
+fd_status fd_set_sponge_vmax(fd_model *m, double vmax);
+
 /* Point source at (ix, iy, iz) with signature S(t_n) = wavelet[n], n < nt
  * (host, copied; steps n >= nt inject nothing).  nt = 0 or wavelet = NULL
  * removes the source.  FD_ERANGE if the point is outside the grid. */
@@ -158,6 +163,29 @@ fd_status fd_get_step(fd_model *m, int *n);
 fd_status fd_get_source_index(fd_model *m, int64_t *idx);
 fd_status fd_get_receiver_indices(fd_model *m, int64_t *out, int cap);
 fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
+
+/* ------------------------------------------------------------------ adjoint
+ *
+ * Building blocks of the reverse-time adjoint (gradient of a trace misfit with
+ * respect to squared slowness m = 1/v^2).  The paper names imaging and
+ * inversion only as uses of its simulator (section 8); the adjoint of the
+ * time step is this library's.  With w = (dt v / h)^2 and damping a, the
+ * adjoint of fd_step for dJ/dtrace^n = g^n is the same step run backwards in
+ * time on psi (a model with the same velocity and no source), with
+ * w g^{k-1} / (1 + a) added at the receivers after step k (fd_inject_receivers),
+ * and dJ/dm = -(1/m) sum_n psi_{n+1} (L' P^n) accumulated by fd_imaging. */
+
+/* Copy P (level n) and, if pold_dev is not NULL, Pold to dense device arrays
+ * [nz][ny][nx] (asynchronous on the model's stream). */
+fd_status fd_get_wavefield_dev(fd_model *m, float *p_dev, float *pold_dev);
+/* Set P, Pold from dense device arrays and the step counter n (asynchronous). */
+fd_status fd_set_wavefield_dev(fd_model *m, const float *p_dev, const float *pold_dev, int n);
+/* Add values_dev[r] * w / (1 + a) to P at each receiver r (values: nrec floats on
+ * the device; the adjoint-source injection). */
+fd_status fd_inject_receivers(fd_model *m, const float *values_dev);
+/* grad_dev += P_adj * (L' p_dev) over dense [nz][ny][nx] device arrays, where
+ * P_adj is the current level of the model adj and L' the stencil sum. */
+fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_dev);
 
 /* --------------------------------------------------------- unfused routines
  *

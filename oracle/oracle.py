@@ -170,7 +170,7 @@ def _dp(a):
 def run(ndim: int, shape, h: float, dt: float, vel, *, sponge_width: int = 0,
         sponge_R: float = 1e-3, src=None, wavelet=None, receivers=None,
         P=None, Pold=None, n0: int = 0, nsteps: int = 0, nthreads: int = 0,
-        coefficients=None):
+        coefficients=None, sponge_vmax=None):
     """Advance the FP64 scheme by ``nsteps`` steps; returns (P, Pold, traces).
 
     shape      (nz, nx) in 2D, (nz, ny, nx) in 3D; arrays are x-fastest.
@@ -181,6 +181,8 @@ def run(ndim: int, shape, h: float, dt: float, vel, *, sponge_width: int = 0,
     P, Pold    initial levels n0 and n0-1 (default zero).
     coefficients  override c_0..c_r (default: the Taylor coefficients); only the
                pin tests pass this.
+    sponge_vmax  velocity that sets the sponge strength (default: the largest
+               velocity of the model).
     """
     lib = _load()
     if ndim == 2:
@@ -199,7 +201,8 @@ def run(ndim: int, shape, h: float, dt: float, vel, *, sponge_width: int = 0,
     Po = np.zeros(npts) if Pold is None else np.array(Pold, dtype=np.float64).reshape(npts).copy()
     etas = [None, None, None]
     if sponge_width > 0:
-        em = sponge_eta_max(float(v.max()), sponge_width, h, sponge_R)
+        vm = float(v.max()) if sponge_vmax is None else float(sponge_vmax)
+        em = sponge_eta_max(vm, sponge_width, h, sponge_R)
         etas = [sponge_profile(nx, sponge_width, em),
                 sponge_profile(ny, sponge_width, em) if ndim == 3 else None,
                 sponge_profile(nz, sponge_width, em)]
@@ -229,3 +232,79 @@ def run(ndim: int, shape, h: float, dt: float, vel, *, sponge_width: int = 0,
     if st != 0:
         raise ValueError(f"fdo_run rejected its arguments (status {st})")
     return Pa.reshape(shape), Po.reshape(shape), traces
+
+
+# ------------------------------------------------------------------------ adjoint
+
+def stencil_sum(P: np.ndarray, coefficients=None) -> np.ndarray:
+    """L'P: sum over the axes of c_0 P + sum_k c_k (P[+k] + P[-k]), zero outside (FP64)."""
+    c = coefficients_f64() if coefficients is None else np.asarray(coefficients, np.float64)
+    r = len(c) - 1
+    pad = np.pad(np.asarray(P, np.float64), r)
+    core = tuple(slice(r, r + n) for n in P.shape)
+    out = np.zeros(P.shape, np.float64)
+    for ax in range(P.ndim):
+        out += c[0] * P
+        for k in range(1, r + 1):
+            up = list(core)
+            dn = list(core)
+            up[ax] = slice(r + k, r + k + P.shape[ax])
+            dn[ax] = slice(r - k, r - k + P.shape[ax])
+            out += c[k] * (pad[tuple(up)] + pad[tuple(dn)])
+    return out
+
+
+def misfit_gradient(ndim: int, shape, h: float, dt: float, vel, *, sponge_width: int = 0,
+                    sponge_R: float = 1e-3, src=None, wavelet=None, receivers=None, nsteps: int = 0,
+                    observed=None, sponge_vmax=None):
+    """J = 1/2 sum_n |d^n - observed^n|^2 and dJ/dm (m = 1/v^2), FP64, by the discrete adjoint.
+
+    The forward recurrence (1+a) P^{n+1} = 2P^n - (1-a) P^{n-1} + W L'P^n + (1+a) s^n e_src,
+    d^n = R P^{n+1}, W = diag((dt v / h)^2) has, for g^n = d^n - observed^n, the adjoint
+    (with psi = W lambda / (1+a))
+        (1+a) psi_k = 2 psi_{k+1} - (1-a) psi_{k+2} + W L'psi_{k+1} + W R^T g^{k-1},
+    k = nt .. 1, psi_{nt+1} = psi_{nt+2} = 0, and the gradient
+        dJ/dm = -(1/m) sum_{n=0}^{nt-1} psi_{n+1} L'P^n.
+    The damping a is held fixed (its strength comes from sponge_vmax).  Every
+    forward level is kept, so this is for small grids.  Returns (J, grad_m, traces).
+    """
+    v = np.asarray(vel, np.float64).reshape(shape)
+    vmax = float(v.max()) if sponge_vmax is None else float(sponge_vmax)
+    rec = np.asarray(receivers, np.int64).reshape(-1, 3)
+    P = np.zeros(shape)
+    Pold = np.zeros(shape)
+    levels = [P.copy()]                        # P^0 .. P^{nt-1}
+    traces = np.zeros((nsteps, len(rec)))
+    for n in range(nsteps):
+        P, Pold, tr = run(ndim, shape, h, dt, v, sponge_width=sponge_width, sponge_R=sponge_R, src=src,
+                          wavelet=wavelet, receivers=rec, P=P, Pold=Pold, n0=n, nsteps=1, sponge_vmax=vmax)
+        traces[n] = tr[0]
+        if n + 1 < nsteps:
+            levels.append(P.copy())
+    g = traces - np.asarray(observed, np.float64)
+    J = 0.5 * float(np.sum(g * g))
+    # receiver points and their w / (1 + a)
+    w = (dt * v / h) ** 2
+    a = np.zeros(shape)
+    if sponge_width > 0:
+        em = sponge_eta_max(vmax, sponge_width, h, sponge_R)
+        a = a + dt * sponge_profile(shape[-1], sponge_width, em)
+        a = a + dt * sponge_profile(shape[0], sponge_width, em).reshape((shape[0],) + (1,) * (ndim - 1))
+        if ndim == 3:
+            a = a + dt * sponge_profile(shape[1], sponge_width, em).reshape((1, shape[1], 1))
+    if ndim == 2:
+        pts = (rec[:, 2], rec[:, 0])
+    else:
+        pts = (rec[:, 2], rec[:, 1], rec[:, 0])
+    scale = w[pts] / (1.0 + a[pts])
+    psi = np.zeros(shape)         # psi_{k+1}
+    psi_old = np.zeros(shape)     # psi_{k+2}
+    acc = np.zeros(shape)
+    for k in range(nsteps, 0, -1):
+        nxt, _, _ = run(ndim, shape, h, dt, v, sponge_width=sponge_width, sponge_R=sponge_R,
+                        P=psi, Pold=psi_old, nsteps=1, sponge_vmax=vmax)
+        np.add.at(nxt, pts, scale * g[k - 1])
+        psi_old, psi = psi, nxt
+        acc += psi * stencil_sum(levels[k - 1])
+    m = 1.0 / (v * v)
+    return J, -acc / m, traces

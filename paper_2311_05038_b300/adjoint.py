@@ -1,0 +1,149 @@
+"""Reverse-time adjoint: gradient of a trace misfit with respect to squared slowness.
+
+``Propagate.apply(m, geometry)`` maps the squared slowness m = 1/v^2 (a CUDA
+tensor shaped like the grid) to the traces [nt][nrec] of one shot, running the
+fused step kernels of libfd; its backward is the discrete adjoint of that time
+step.  With w = (dt v / h)^2, damping a and g^n = dJ/dtrace^n, the adjoint
+wavefield psi obeys the same damped leapfrog backwards in time,
+
+    (1 + a) psi_k = 2 psi_{k+1} - (1 - a) psi_{k+2} + W L' psi_{k+1} + W R^T g^{k-1},
+
+so it advances with ``fd_step`` on a second model with the same velocity and no
+source, the receiver terms entering through ``fd_inject_receivers``; the
+gradient is dJ/dm = -(1/m) sum_n psi_{n+1} L'P^n, accumulated by ``fd_imaging``.
+The sponge's damping is held fixed.
+
+Memory is bounded by checkpointing: the forward pass keeps (P, Pold) every
+``checkpoint_every`` steps; the backward pass walks the segments last to first,
+recomputes each segment's forward levels from its checkpoint into a buffer of
+``checkpoint_every`` fields, and runs the adjoint through it.  The forward
+work is therefore done twice.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import fd
+
+
+@dataclass
+class Geometry:
+    """One shot's fixed inputs (everything but the model)."""
+    ndim: int
+    shape: tuple
+    h: float
+    dt: float
+    nt: int
+    src: tuple
+    wavelet: np.ndarray
+    receivers: np.ndarray
+    sponge_width: int = 0
+    sponge_R: float = 1e-3
+    sponge_vmax: float | None = None
+    checkpoint_every: int = 50
+
+    @classmethod
+    def from_shot(cls, shot, checkpoint_every=50, sponge_vmax=None):
+        return cls(shot.ndim, tuple(shot.shape), shot.h, shot.dt, shot.nt, shot.src, shot.wavelet, shot.receivers,
+                   shot.sponge_width, shot.sponge_R, sponge_vmax, checkpoint_every)
+
+
+def _model(torch, geo: Geometry, v, with_source: bool):
+    stream = torch.cuda.current_stream()
+    m = fd.Model(geo.ndim, geo.shape, geo.h, geo.dt, v.contiguous(), geo.sponge_width, geo.sponge_R, stream=stream)
+    if geo.sponge_vmax is not None:
+        fd.fd_set_sponge_vmax(m.handle, geo.sponge_vmax)
+    if with_source:
+        m.set_source(geo.src, geo.wavelet)
+    m.set_receivers(geo.receivers)
+    return m
+
+
+class Propagate:
+    """torch.autograd.Function: squared slowness -> traces, with the adjoint as backward."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, m, geo: Geometry):
+        if cls._fn is None:
+            cls._fn = _make_function()
+        return cls._fn.apply(m, geo)
+
+
+def _make_function():
+    import torch
+
+    class _Propagate(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, m, geo):
+            if not m.is_cuda:
+                raise ValueError("m must be a CUDA tensor")
+            v = torch.rsqrt(m.detach().to(torch.float32)).contiguous()
+            model = _model(torch, geo, v, with_source=True)
+            nrec = len(geo.receivers)
+            traces = torch.zeros((geo.nt, nrec), device=m.device, dtype=torch.float32)
+            fd.fd_reset(model.handle)
+            fd.fd_set_trace_buffer(model.handle, traces, geo.nt)
+            K = max(1, int(geo.checkpoint_every))
+            ckpts = []
+            for n0 in range(0, geo.nt, K):
+                P = torch.empty(geo.shape, device=m.device, dtype=torch.float32)
+                Po = torch.empty_like(P)
+                fd.fd_get_wavefield_dev(model.handle, P, Po)
+                ckpts.append((P, Po))
+                fd.fd_step(model.handle, min(K, geo.nt - n0))
+            fd.fd_synchronize(model.handle)
+            ctx.geo = geo
+            ctx.model = model
+            ctx.v = v
+            ctx.ckpts = ckpts
+            ctx.save_for_backward(m)
+            return traces
+
+        @staticmethod
+        def backward(ctx, grad_traces):
+            (m,) = ctx.saved_tensors
+            geo, model, v = ctx.geo, ctx.model, ctx.v
+            g = grad_traces.detach().to(torch.float32).contiguous()
+            K = max(1, int(geo.checkpoint_every))
+            adj = _model(torch, geo, v, with_source=False)
+            fd.fd_reset(adj.handle)
+            fd.fd_set_trace_buffer(model.handle, None, 0)       # recompute without recording
+            seg = torch.empty((K,) + tuple(geo.shape), device=m.device, dtype=torch.float32)
+            acc = torch.zeros(geo.shape, device=m.device, dtype=torch.float32)
+            for s in range(len(ctx.ckpts) - 1, -1, -1):
+                n0 = s * K
+                n1 = min(n0 + K, geo.nt)
+                P, Po = ctx.ckpts[s]
+                fd.fd_set_wavefield_dev(model.handle, P, Po, n0)
+                seg[0].copy_(P)
+                for j in range(1, n1 - n0):
+                    fd.fd_step(model.handle, 1)
+                    fd.fd_get_wavefield_dev(model.handle, seg[j])
+                for k in range(n1, n0, -1):
+                    fd.fd_step(adj.handle, 1)                     # psi_k from psi_{k+1}, psi_{k+2}
+                    fd.fd_inject_receivers(adj.handle, g[k - 1])  # + w g^{k-1} / (1 + a)
+                    fd.fd_imaging(adj.handle, seg[k - 1 - n0], acc)
+            fd.fd_synchronize(adj.handle)
+            adj.close()
+            model.close()
+            ctx.model = None
+            ctx.ckpts = None
+            grad_m = -(acc / m.detach().to(torch.float32)).to(m.dtype)
+            return grad_m, None
+
+    return _Propagate
+
+
+def misfit_and_gradient(m, geo: Geometry, observed):
+    """J = 1/2 |traces(m) - observed|^2 (accumulated in FP64) and dJ/dm."""
+    import torch
+    mm = m.detach().clone().requires_grad_(True)
+    tr = Propagate.apply(mm, geo)
+    r = tr - observed
+    J = 0.5 * (r.double() * r.double()).sum()
+    J.backward()
+    return float(J.detach()), mm.grad

@@ -210,6 +210,24 @@ static void free_model(fd_model *m)
     delete m;
 }
 
+// Damping profiles a = dt * eta per axis from the sponge strength of the model
+// (its largest velocity, or the velocity fixed by fd_set_sponge_vmax).
+static fd_status upload_damping(fd_model *m)
+{
+    const int W = m->d.sponge_width;
+    m->has_sponge = W > 0;
+    const double vref = m->sponge_vref > 0.0 ? m->sponge_vref : (double)m->vmax;
+    const double eta_max = W > 0 ? 3.0 * vref * std::log(1.0 / m->d.sponge_R) / (2.0 * W * m->d.h) : 0.0;
+    auto pax = damping_profile(m->nx, m->px, W, eta_max, m->d.dt);
+    auto pay = damping_profile(m->ny, m->ny, m->d.ndim == 3 ? W : 0, eta_max, m->d.dt);
+    auto paz = damping_profile(m->nz, m->nz, W, eta_max, m->d.dt);
+    FD_CUDA(cudaMemcpyAsync(m->ax, pax.data(), pax.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge x");
+    FD_CUDA(cudaMemcpyAsync(m->ay, pay.data(), pay.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge y");
+    FD_CUDA(cudaMemcpyAsync(m->az, paz.data(), paz.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge z");
+    FD_CUDA(cudaStreamSynchronize(m->stream), "velocity setup");
+    return FD_OK;
+}
+
 // Load a dense velocity (host or device) into a staging copy, check it, and on
 // success turn it into w and the sponge profiles.  Leaves the model untouched
 // on failure.
@@ -252,17 +270,7 @@ static fd_status load_velocity(fd_model *m, const float *v, cudaMemcpyKind kind)
         return cuda_fail(e, "computing w");
     }
     m->vmax = vmax;
-    const int W = m->d.sponge_width;
-    m->has_sponge = W > 0;
-    const double eta_max = W > 0 ? 3.0 * (double)vmax * std::log(1.0 / m->d.sponge_R) / (2.0 * W * m->d.h) : 0.0;
-    auto pax = damping_profile(m->nx, m->px, W, eta_max, m->d.dt);
-    auto pay = damping_profile(m->ny, m->ny, m->d.ndim == 3 ? W : 0, eta_max, m->d.dt);
-    auto paz = damping_profile(m->nz, m->nz, W, eta_max, m->d.dt);
-    FD_CUDA(cudaMemcpyAsync(m->ax, pax.data(), pax.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge x");
-    FD_CUDA(cudaMemcpyAsync(m->ay, pay.data(), pay.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge y");
-    FD_CUDA(cudaMemcpyAsync(m->az, paz.data(), paz.size() * 4, cudaMemcpyHostToDevice, m->stream), "sponge z");
-    FD_CUDA(cudaStreamSynchronize(m->stream), "velocity setup");
-    return FD_OK;
+    return upload_damping(m);
 }
 
 static fd_status create(const fd_grid_desc *desc, const float *v, cudaMemcpyKind kind, void *stream,
@@ -418,6 +426,15 @@ extern "C" fd_status fd_set_velocity_dev(fd_model *m, const float *v_dev)
 {
     NEED_MODEL(m);
     return load_velocity(m, v_dev, cudaMemcpyDeviceToDevice);
+}
+
+extern "C" fd_status fd_set_sponge_vmax(fd_model *m, double vmax)
+{
+    NEED_MODEL(m);
+    if (!(vmax >= 0.0) || !std::isfinite(vmax))
+        return fail(FD_EINVAL, "sponge velocity must be finite and >= 0");
+    m->sponge_vref = vmax;
+    return upload_damping(m);
 }
 
 static bool inside(const fd_model *m, int ix, int iy, int iz)

@@ -29,6 +29,7 @@ struct fd_model {
     float *ax = nullptr, *ay = nullptr, *az = nullptr;
     int has_sponge = 0;
     float vmax = 0.f;
+    double sponge_vref = 0.0;  // velocity fixing the sponge strength (0: the model's vmax)
     int *d_err = nullptr;
     unsigned *d_stats = nullptr;
 

@@ -39,6 +39,8 @@ EXPORTS = [
     "fd_get_damping_profile", "fd_kernel_launch_count", "fd_last_error",
     "fd_batch_create", "fd_batch_destroy", "fd_batch_set_tuning", "fd_batch_get_tuning", "fd_batch_step",
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
+    "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
+    "fd_set_sponge_vmax",
 ]
 
 
@@ -102,6 +104,11 @@ _SIGS = {
     "fd_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(fd_batch_tuning)]),
     "fd_batch_step_noalloc": (_i, [ctypes.POINTER(_vp), _i, _i]),
     "fd_routine": (_i, [_vp, _i]),
+    "fd_get_wavefield_dev": (_i, [_vp, _vp, _vp]),
+    "fd_set_wavefield_dev": (_i, [_vp, _vp, _vp, _i]),
+    "fd_inject_receivers": (_i, [_vp, _vp]),
+    "fd_imaging": (_i, [_vp, _vp, _vp]),
+    "fd_set_sponge_vmax": (_i, [_vp, ctypes.c_double]),
     "fd_step_unfused": (_i, [_vp, _i]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
@@ -187,6 +194,10 @@ def fd_set_velocity_ptr(m: int, host_ptr: int):
 
 def fd_set_velocity_dev(m: int, v_dev):
     _check(_lib.fd_set_velocity_dev(m, _dev_ptr(v_dev)), "fd_set_velocity_dev")
+
+
+def fd_set_sponge_vmax(m: int, vmax: float):
+    _check(_lib.fd_set_sponge_vmax(m, float(vmax)), "fd_set_sponge_vmax")
 
 
 def fd_set_source(m: int, ix: int, iy: int, iz: int, wavelet=None):
@@ -335,6 +346,23 @@ def fd_routine(m: int, routine: int):
 
 def fd_step_unfused(m: int, nsteps: int):
     _check(_lib.fd_step_unfused(m, int(nsteps)), "fd_step_unfused")
+
+
+def fd_get_wavefield_dev(m: int, p_dev, pold_dev=None):
+    _check(_lib.fd_get_wavefield_dev(m, _dev_ptr(p_dev), None if pold_dev is None else _dev_ptr(pold_dev)),
+           "fd_get_wavefield_dev")
+
+
+def fd_set_wavefield_dev(m: int, p_dev, pold_dev, n: int = 0):
+    _check(_lib.fd_set_wavefield_dev(m, _dev_ptr(p_dev), _dev_ptr(pold_dev), int(n)), "fd_set_wavefield_dev")
+
+
+def fd_inject_receivers(m: int, values_dev):
+    _check(_lib.fd_inject_receivers(m, _dev_ptr(values_dev)), "fd_inject_receivers")
+
+
+def fd_imaging(adj: int, p_dev, grad_dev):
+    _check(_lib.fd_imaging(adj, _dev_ptr(p_dev), _dev_ptr(grad_dev)), "fd_imaging")
 
 
 # ------------------------------------------------------------------ convenience

@@ -239,3 +239,26 @@ def serving_3d_shot(i: int, n: int, nt: int, seed: int = 4, sponge_width: int = 
     return Shot(ndim=3, shape=shape, h=h, dt=dt, nt=nt, vel=vel, src=src,
                 wavelet=ricker(nt, dt, f), receivers=rec, sponge_width=sponge_width,
                 name=f"3d-serve-{n}-{nt}-shot{i}")
+
+
+def adjoint_3d(n: int = 256, nt: int = 1500, nshots: int = 8, seed: int = 5, sponge_width: int = 20):
+    """The adjoint workload: smoothed random velocity in [1500, 4000] (GRF, 200 m),
+    nshots surface shots at seeded positions, and the true model with a +5 %
+    Gaussian anomaly (std 150 m) at the centre.  Returns (shots, v_true)."""
+    shape = (n, n, n)
+    vel = grf_velocity(shape, corr_cells=20.0, vmin=1500.0, vmax=4000.0, seed=seed)
+    h, f = 10.0, 10.0
+    dt = courant_dt(h, 4000.0 * 1.05)
+    rng = np.random.default_rng(seed)
+    idx = np.indices(shape, dtype=np.float64)
+    r2 = sum((idx[i] - (n - 1) / 2.0) ** 2 for i in range(3)) * h * h
+    v_true = (vel.astype(np.float64) * (1.0 + 0.05 * np.exp(-r2 / (2 * 150.0 ** 2)))).astype(np.float32)
+    xs = range(n // 8, n - n // 8, 4)
+    rec = np.array([(ix, iy, sponge_width + 5) for iy in xs for ix in xs], dtype=np.int32)
+    shots = []
+    for i in range(nshots):
+        sx, sy = (int(q) for q in rng.integers(n // 4, 3 * n // 4, 2))
+        shots.append(Shot(ndim=3, shape=shape, h=h, dt=dt, nt=nt, vel=vel, src=(sx, sy, sponge_width + 8),
+                          wavelet=ricker(nt, dt, f), receivers=rec, sponge_width=sponge_width,
+                          name=f"3d-adjoint-{n}-{nt}-shot{i}"))
+    return shots, v_true
