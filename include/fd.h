@@ -250,6 +250,12 @@ fd_status fd_batch_get_tuning(fd_batch *b, fd_batch_tuning *t);
  * nsteps_each is NULL), exactly as fd_step would, traces included.  Blocks
  * until done; returns FD_ETIMEOUT if a bounded device wait gave up. */
 fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each);
+/* Test hook for the failure path: from the next fd_batch_step on, work item
+ * stalled_item (0-based in the batch's (shot, tile) order; -1 clears it) never
+ * runs, so its neighbours' bounded waits run out and the call returns
+ * FD_ETIMEOUT with the context still usable.  After FD_ETIMEOUT the shots'
+ * wavefields are undefined until reset. */
+fd_status fd_batch_set_fault(fd_batch *b, int stalled_item);
 /* Time every tuning candidate on trial_steps steps of this batch, keep the
  * fastest (cached per batch shape for the process) and write it to best.  The
  * trial steps change the models' state: call fd_reset or fd_run_shot after. */

@@ -77,6 +77,7 @@ struct BatchParams {
     BatchState *state;
     float c1, c2, c3, c4;
     int *err;
+    int stall_item;        // test hook: this item never runs (-1: none)
 };
 
 // What the consumers need about the item in a ring stage; written by the
@@ -112,6 +113,21 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// AND of v over the nthreads threads of named barrier id (all of them must call it).
+__device__ __forceinline__ bool named_and(int id, int nthreads, bool v)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((int)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void named_sync(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -129,7 +145,7 @@ __device__ __forceinline__ int ld_relaxed(const int *p)
 // fence orders the later reads after them.  False if the cycle budget runs
 // out or *abort is raised.
 __device__ __forceinline__ bool wait_deps(const int *counters, int i, const int (&nb)[4], int v,
-                                          volatile int *abort)
+                                          volatile int *abort, const volatile int *err)
 {
     long long t0 = -1;
     for (;;) {
@@ -142,8 +158,8 @@ __device__ __forceinline__ bool wait_deps(const int *counters, int i, const int 
             break;
         if (t0 < 0)
             t0 = clock64();
-        else if (*abort || clock64() - t0 > kWaitLimitCycles)
-            return false;
+        else if (*abort || *err || clock64() - t0 > kWaitLimitCycles)
+            return false;    // own budget spent, or another CTA already gave up
         __nanosleep(32);
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
@@ -208,9 +224,9 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
                         if (i + (int)gridDim.x < ie)
                             nxt = bp.items[i + gridDim.x];   // prefetch the next descriptor
                         const ShotDesc &sd = bp.shots[it.shot];
-                        if (cs >= sd.target)
+                        if (cs >= sd.target || i == bp.stall_item)
                             continue;
-                        good = wait_deps(bp.counters, i, it.nb, cs, &s_abort);
+                        good = wait_deps(bp.counters, i, it.nb, cs, &s_abort, bp.err);
                         const int slot = k % S;
                         if (good && k >= S)
                             good = mbar_wait(&empty[slot], ((k / S) - 1) & 1, &s_abort);
@@ -271,7 +287,9 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
         const int tz = tid / QX;
         for (int k = 0;; ++k) {
             const int slot = k % S;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (k / S) & 1, &s_abort))) {
+            // every consumer thread takes the same decision, so none is left
+            // waiting at the item's named barriers after the others gave up
+            if (!named_and(1, NC, mbar_wait(&full[slot], (k / S) & 1, &s_abort))) {
                 raise_error(bp.err, &s_abort, kDevErrTimeout);
                 break;
             }
@@ -380,6 +398,7 @@ struct fd_batch {
     int nitems = 0, ngroups = 0, grid = 0;
     cudaGraphExec_t exec = nullptr;
     std::vector<ShotDesc> shots;   // host copy (tensor maps, pointers)
+    int stall_item = -1;           // fd_batch_set_fault
 };
 
 static void free_tables(fd_batch *b)
@@ -561,6 +580,18 @@ extern "C" fd_status fd_batch_set_tuning(fd_batch *b, const fd_batch_tuning *t)
     return FD_OK;
 }
 
+extern "C" fd_status fd_batch_set_fault(fd_batch *b, int stalled_item)
+{
+    if (!b || stalled_item < -1)
+        return fail(FD_EINVAL, "fd_batch_set_fault: bad arguments");
+    b->stall_item = stalled_item;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return FD_OK;
+}
+
 extern "C" fd_status fd_batch_get_tuning(fd_batch *b, fd_batch_tuning *t)
 {
     if (!b || !t)
@@ -661,6 +692,7 @@ extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_ea
             p.c3 = w4[2];
             p.c4 = w4[3];
             p.err = b->d_err;
+            p.stall_item = b->stall_item;
             fd_status st = capture_graph(b, p);
             if (st)
                 return st;
@@ -927,6 +959,7 @@ extern "C" fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels,
         p.c3 = w4[2];
         p.c4 = w4[3];
         p.err = reinterpret_cast<int *>(dbase + offsetof(NoAllocScratch, err));
+        p.stall_item = -1;
         int per_sm = 0, sms = 0;
         FD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.threads, v.smem), "occupancy");
         FD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");

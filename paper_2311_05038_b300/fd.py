@@ -40,7 +40,7 @@ EXPORTS = [
     "fd_batch_create", "fd_batch_destroy", "fd_batch_set_tuning", "fd_batch_get_tuning", "fd_batch_step",
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
-    "fd_set_sponge_vmax",
+    "fd_set_sponge_vmax", "fd_batch_set_fault",
 ]
 
 
@@ -109,6 +109,7 @@ _SIGS = {
     "fd_inject_receivers": (_i, [_vp, _vp]),
     "fd_imaging": (_i, [_vp, _vp, _vp]),
     "fd_set_sponge_vmax": (_i, [_vp, ctypes.c_double]),
+    "fd_batch_set_fault": (_i, [_vp, _i]),
     "fd_step_unfused": (_i, [_vp, _i]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
@@ -323,6 +324,10 @@ def fd_batch_step(b: int, nsteps: int, nsteps_each=None):
         each = np.ascontiguousarray(nsteps_each, dtype=np.int32)
         arr = each.ctypes.data_as(_ip)
     _check(_lib.fd_batch_step(b, int(nsteps), arr), "fd_batch_step")
+
+
+def fd_batch_set_fault(b: int, stalled_item: int):
+    _check(_lib.fd_batch_set_fault(b, int(stalled_item)), "fd_batch_set_fault")
 
 
 def fd_batch_autotune(b: int, trial_steps: int) -> dict:

@@ -122,3 +122,26 @@ def test_batch_rejects_3d_models(fdlib):
         with pytest.raises(fdlib.FDError) as e:
             fdlib.fd_batch_create([m.handle])
         assert e.value.status == fdlib.FD_EINVAL
+
+
+def test_stalled_item_times_out_and_context_survives(fdlib):
+    """A tile whose completion is withheld makes its neighbours' bounded waits run
+    out: fd_batch_step returns FD_ETIMEOUT (no fault, no hang), and the same
+    context then runs a clean batch whose results equal the solo runs."""
+    import time
+    shots = small_shots(n=3, nt=40, seed=55)
+    models = [fdlib.Model.from_shot(s) for s in shots]
+    with fdlib.Batch(models) as b:
+        b.set_tuning(tile=0, steps_per_launch=40, ctas_per_sm=0, group_mb=0)
+        fdlib.fd_batch_set_fault(b.handle, 1)
+        t0 = time.perf_counter()
+        with pytest.raises(fdlib.FDError) as e:
+            b.run_shots([40, 40, 40])
+        assert e.value.status == fdlib.FD_ETIMEOUT
+        assert time.perf_counter() - t0 < 30
+        fdlib.fd_batch_set_fault(b.handle, -1)
+        b.run_shots([40, 40, 40])
+        got = [(m.wavefield(with_old=True), m.traces(40)) for m in models]
+    for m in models:
+        m.close()
+    assert_same(got, solo(fdlib, shots, [40, 40, 40]))
