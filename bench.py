@@ -50,8 +50,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--n", type=int, default=512, help="cube side")
-    ap.add_argument("--nt", type=int, default=1000, help="time steps per shot")
+    ap.add_argument("--grid", "--n", dest="n", type=int, default=512, help="cube side")
+    ap.add_argument("--time-steps", "--nt", dest="nt", type=int, default=1000, help="time steps per shot")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -160,6 +160,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(dist, x: float, device="cpu") -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, elapsed_max: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / elapsed_max
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -224,7 +239,7 @@ def run_reference(args, dist, rank, world):
               f"FP64 oracle (plain C loop, OpenMP over z)")
     line = {
         "impl": "reference", "metric": "Gpt-updates/s", "value": value, "unit": "Gupd/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": shot.name, "grid": list(shot.shape), "time_steps_per_bench_step": per_step,
@@ -450,13 +465,6 @@ def run_b300(args, dist, rank, local, world):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- device-resident timed region
     for _ in range(args.warmup):
         model.run_shot(shot.nt, traces)
@@ -477,8 +485,8 @@ def run_b300(args, dist, rank, local, world):
     launches = fd.fd_kernel_launch_count() - launches0
     fd.fd_synchronize(model.handle)
     barrier()
-    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-    value = world * args.steps * shot.nt * npts / elapsed / 1e9
+    elapsed = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, "cuda")
+    value = replica_throughput(args.steps * shot.nt * npts, world, elapsed) / 1e9
     step_launches = args.steps * shot.nt
     avg_launch_s = ev0.elapsed_time(ev1) / 1e3 / step_launches
     achieved = BYTES_PER_UPDATE * npts / avg_launch_s / 1e9
@@ -509,7 +517,7 @@ def run_b300(args, dist, rank, local, world):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
         h2d = shot.vel.nbytes + shot.wavelet.nbytes + rec.nbytes
         d2h = shot.nt * nrec * 4
         e2e = {"value": world * args.steps * shot.nt * npts / el / 1e9, "unit": "Gupd/s",
