@@ -109,7 +109,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // FP32 tensor map over a pitched field: rank 2 ([nz][px], extents nx, nz) or
 // rank 3 ([nz][ny][px], extents nx, ny, nz), with the given box.
-bool fdk::make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by)
+bool fdk::make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by,
+                   int bz)
 {
     auto fn = encode_fn();
     if (!fn)
@@ -135,7 +136,7 @@ bool fdk::make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int 
         strides[1] = (cuuint64_t)px * ny * 4;
         box[0] = bx;
         box[1] = by;
-        box[2] = 1;
+        box[2] = bz;
     }
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -353,14 +354,15 @@ static fd_status create(const fd_grid_desc *desc, const float *v, cudaMemcpyKind
     bool ok = true;
     for (int i = 0; i < 2; ++i) {
         if (ndim == 3) {
-            ok = ok && make_map(&m->halo_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3 + 8, kTY3 + 8);
-            ok = ok && make_map(&m->tile_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3);
+            ok = ok && make_map(&m->halo_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3 + 8, kTY3 + 8,
+                                kPlanes3);
+            ok = ok && make_map(&m->tile_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3, kPlanes3);
         } else {
             ok = ok && make_map(&m->halo_map[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, kTX2 + 8, kTZ2 + 8);
             ok = ok && make_map(&m->tile_map[i], m->buf[i], 2, m->nx, 1, m->nz, m->px, kTX2, kTZ2);
         }
     }
-    ok = ok && (ndim == 3 ? make_map(&m->w_map, m->w, 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3)
+    ok = ok && (ndim == 3 ? make_map(&m->w_map, m->w, 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3, kPlanes3)
                           : make_map(&m->w_map, m->w, 2, m->nx, 1, m->nz, m->px, kTX2, kTZ2));
     if (!ok)
         return bail(fail(FD_ECUDA, "cuTensorMapEncodeTiled failed"));

@@ -14,7 +14,8 @@ namespace fdk {
 constexpr int kRadius = 4;
 
 // 3D step: a CTA owns a kTX3 x kTY3 column of the (x, y) plane and marches
-// along z through bz planes, fed by two TMA rings in shared memory.
+// along z through bz planes, fed by two TMA rings in shared memory whose
+// stages hold kPlanes3 consecutive planes each.
 // Compile-time knobs (defaults are the tuned configuration).
 #ifndef FD_TX3
 #define FD_TX3 32
@@ -23,18 +24,23 @@ constexpr int kRadius = 4;
 #define FD_TY3 32
 #endif
 #ifndef FD_STAGESP3
-#define FD_STAGESP3 11
+#define FD_STAGESP3 5
 #endif
 #ifndef FD_STAGEST3
-#define FD_STAGEST3 4
+#define FD_STAGEST3 2
+#endif
+#ifndef FD_QGROUP3
+#define FD_QGROUP3 2
 #endif
 #ifndef FD_MINB3
 #define FD_MINB3 2
 #endif
 constexpr int kTX3 = FD_TX3;
 constexpr int kTY3 = FD_TY3;
-constexpr int kStagesP3 = FD_STAGESP3;   // haloed P planes in flight
-constexpr int kStagesT3 = FD_STAGEST3;   // Pold + w tiles in flight
+constexpr int kPlanes3 = 2;              // z planes per TMA stage (the box depth)
+constexpr int kStagesP3 = FD_STAGESP3;   // haloed P stages in flight
+constexpr int kStagesT3 = FD_STAGEST3;   // Pold + w stages in flight
+constexpr int kGroup3 = FD_QGROUP3;      // stages per unrolled z-queue rotation
 constexpr int kMinBlocks3 = FD_MINB3;
 constexpr int kThreads3 = kTX3 / 4 * kTY3;
 
@@ -84,8 +90,9 @@ cudaError_t launch_compute_w(const float *v, float *w, int nx, size_t rows, int 
 
 // Host helpers shared by the C ABI translation units.
 // FP32 tensor map over a pitched field: rank 2 ([nz][px], extents nx, nz) or
-// rank 3 ([nz][ny][px], extents nx, ny, nz), with box bx x by (x 1).
-bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by);
+// rank 3 ([nz][ny][px], extents nx, ny, nz), with box bx x by (x bz planes).
+bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by,
+              int bz = 1);
 // Record a message for fd_last_error() and return st.
 fd_status fail(fd_status st, const char *fmt, ...);
 fd_status cuda_fail(cudaError_t e, const char *what);

@@ -34,18 +34,21 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 // A CTA owns the column [x0, x0+TX) x [y0, y0+TY) and output planes [z0, z1);
 // each of its TX/4*TY threads computes 4 consecutive x points of one row.
 //
-// Two TMA rings feed it.  The P ring (SP slots) holds haloed P planes: stage k
-// is plane z0-4+k, k = 0 .. nb+7.  The T ring (ST slots) holds the Pold and w
-// tiles of output plane z0+t, t = 0 .. nb-1.  Computing plane z = z0+j needs P
-// stages j+4 (x/y neighbours, the plane itself) and j+8 (the newest plane; its
-// centre enters a 9-deep register queue that supplies the z neighbours) and T
-// stage j.  Afterwards the warp frees P stage j+4 and T stage j.
+// Two TMA rings feed it, each stage a box two planes deep.  Counting "relative
+// planes" from z0-4, P stage k (SP slots) holds the haloed P planes 2k and
+// 2k+1; T stage t (ST slots) holds the Pold and w tiles of output planes
+// z0+2t and z0+2t+1.  Body i computes output planes j = 2i and j+1: their x/y
+// neighbours come from P stage i+2, the two newest planes (relative j+8, j+9)
+// from P stage i+4 enter a register queue that supplies the z neighbours, and
+// Pold, w from T stage i.  Afterwards the warp frees P stage i+2 and T stage i.
+// Pairing planes halves the per-plane cost of the barrier probes, releases and
+// ring bookkeeping.
 //
 // There is no producer thread: a per-slot shared counter finds the last warp to
 // free a slot, and that warp issues the slot's next stage at once, so loads run
-// SP-5 P stages and ST-1 T stages ahead of the slowest warp without anyone
-// blocking.  The only waits are the bounded waits on the full barriers.
-template <int TX, int TY, int SP, int ST>
+// ahead of the slowest warp without anyone blocking.  The only waits are the
+// bounded waits on the full barriers.
+template <int TX, int TY, int SP, int ST, int G>
 __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -57,17 +60,21 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     constexpr int HY = TY + 8;
     constexpr int PBOX = HX * HY;
     constexpr int TBOX = TX * TY;
-    constexpr uint32_t BYTES_P = PBOX * 4;
-    constexpr uint32_t BYTES_T = TBOX * 4;
+    constexpr int PST = 2 * PBOX;
+    constexpr int TST = 4 * TBOX;
+    constexpr uint32_t BYTES_P = PST * 4;
+    constexpr uint32_t BYTES_T = TST * 4;
+    constexpr int QN = 8 + 2 * G;
     static_assert(NT % 32 == 0, "threads must fill warps");
     static_assert((PBOX * 4) % 128 == 0 && (TBOX * 4) % 128 == 0, "boxes keep 128-byte alignment");
-    static_assert(SP >= 9, "P ring must hold planes z..z+4 and run ahead");
+    static_assert(kPlanes3 == 2, "bodies compute the two planes of a stage");
+    static_assert(SP >= 4, "P ring must hold stages i+2 .. i+4 and run ahead");
     static_assert(ST >= 2, "T ring must run ahead");
 
     extern __shared__ __align__(128) unsigned char smem[];
     float *sP = reinterpret_cast<float *>(smem);
-    float *sT = sP + SP * PBOX;                       // [ST][Pold tile, w tile]
-    uint64_t *fullP = reinterpret_cast<uint64_t *>(sT + ST * 2 * TBOX);
+    float *sT = sP + SP * PST;
+    uint64_t *fullP = reinterpret_cast<uint64_t *>(sT + ST * TST);
     uint64_t *fullT = fullP + SP;
     unsigned *relP = reinterpret_cast<unsigned *>(fullT + ST);
     unsigned *relT = relP + SP;
@@ -80,19 +87,20 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const int z0 = blockIdx.y * prm.bz;
     const int z1 = min(prm.nz, z0 + prm.bz);
     const int nb = z1 - z0;
-    const int nP = nb + 8;
+    const int nbh = (nb + 1) >> 1;
+    const int nPS = nbh + 4;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
 
     auto issueP = [&](int k, int slot) {
         mbar_arrive_expect_tx(&fullP[slot], BYTES_P);
-        tma_load_3d(sP + slot * PBOX, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + k);
+        tma_load_3d(sP + slot * PST, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + 2 * k);
         atomicAdd(&s_issuedP, 1);
     };
     auto issueT = [&](int t, int slot) {
-        mbar_arrive_expect_tx(&fullT[slot], 2 * BYTES_T);
-        tma_load_3d(sT + (2 * slot) * TBOX, &tmOld, &fullT[slot], x0, y0, z0 + t);
-        tma_load_3d(sT + (2 * slot + 1) * TBOX, &tmW, &fullT[slot], x0, y0, z0 + t);
+        mbar_arrive_expect_tx(&fullT[slot], BYTES_T);
+        tma_load_3d(sT + slot * TST, &tmOld, &fullT[slot], x0, y0, z0 + 2 * t);
+        tma_load_3d(sT + slot * TST + 2 * TBOX, &tmW, &fullT[slot], x0, y0, z0 + 2 * t);
         atomicAdd(&s_issuedT, 1);
     };
     // Free P stage k (in slot sp) and, if t >= 0, T stage t (in slot stt); the
@@ -100,11 +108,11 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     auto release = [&](int k, int sp, int t, int stt) {
         __syncwarp();
         if (lane == 0) {
-            if (atomicAdd(&relP[sp], 1u) % NW == NW - 1 && k + SP < nP) {
+            if (atomicAdd(&relP[sp], 1u) % NW == NW - 1 && k + SP < nPS) {
                 fence_proxy_async_shared();
                 issueP(k + SP, sp);
             }
-            if (t >= 0 && atomicAdd(&relT[stt], 1u) % NW == NW - 1 && t + ST < nb) {
+            if (t >= 0 && atomicAdd(&relT[stt], 1u) % NW == NW - 1 && t + ST < nbh) {
                 fence_proxy_async_shared();
                 issueT(t + ST, stt);
             }
@@ -130,9 +138,9 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
         prefetch_tensormap(&tmP);
         prefetch_tensormap(&tmOld);
         prefetch_tensormap(&tmW);
-        for (int k = 0; k < min(SP, nP); ++k)
+        for (int k = 0; k < min(SP, nPS); ++k)
             issueP(k, k);
-        for (int t = 0; t < min(ST, nb); ++t)
+        for (int t = 0; t < min(ST, nbh); ++t)
             issueT(t, t);
     }
 
@@ -142,19 +150,20 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const int ty = tid / QX;
     const int x = x0 + 4 * tx;
     const int y = y0 + ty;
-    const int cP = (ty + 4) * HX + 4 * tx + 4;   // centre float4 within a P box
-    const int cT = ty * TX + 4 * tx;             // float4 within a Pold / w tile
+    const int cP = (ty + 4) * HX + 4 * tx + 4;
+    const int cT = ty * TX + 4 * tx;
     const bool row_ok = y < prm.ny;
 
     float axv[4] = {0.f, 0.f, 0.f, 0.f};
     float ayv = 0.f;
-    float azn = 0.f;   // az of the next output plane
+    float az0 = 0.f, az1 = 0.f;   // az of the current body's two planes
     if (prm.has_sponge) {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             axv[e] = x + e < prm.px ? prm.ax[x + e] : 0.f;
         ayv = row_ok ? prm.ay[y] : 0.f;
-        azn = prm.az[z0];
+        az0 = prm.az[z0];        // profiles are zero-padded well past nz
+        az1 = prm.az[z0 + 1];
     }
     const bool x_band = axv[0] != 0.f || axv[1] != 0.f || axv[2] != 0.f || axv[3] != 0.f;
     const bool src_col = prm.src_on && y == prm.sy && (unsigned)(prm.sx - x) < 4u;
@@ -163,17 +172,18 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     float *const out_col = prm.out + ((size_t)z0 * prm.ny + y) * prm.px + x;
     const size_t plane_stride = (size_t)prm.ny * prm.px;
 
-    // z-neighbour queue, advanced three planes at a time: in the r-th body of a
-    // group of three, Q[i + r] holds the thread's 4 points of plane z-4+i.
-    float4 Q[11];
+    // z queue, advanced G bodies (2G planes) at a time: in the r-th body of a
+    // group, Q[i + 2r] holds relative plane j + i.
+    float4 Q[QN];
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 4; ++k) {
         ok = __all_sync(0xffffffffu, mbar_wait(&fullP[k % SP], (k / SP) & 1, &s_abort));
         if (!ok)
             break;
-        Q[k] = *reinterpret_cast<const float4 *>(sP + (k % SP) * PBOX + cP);
-        if (k < 4)
+        Q[2 * k] = *reinterpret_cast<const float4 *>(sP + (k % SP) * PST + cP);
+        Q[2 * k + 1] = *reinterpret_cast<const float4 *>(sP + (k % SP) * PST + PBOX + cP);
+        if (k < 2)
             release(k, k % SP, -1, 0);
     }
 
@@ -181,26 +191,14 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const float2 NEG1 = make_float2(-1.0f, -1.0f);
     const float2 C1 = make_float2(prm.c1, prm.c1), C2 = make_float2(prm.c2, prm.c2);
     const float2 C3 = make_float2(prm.c3, prm.c3), C4 = make_float2(prm.c4, prm.c4);
-    // ring positions of P stage j+8 (newest), P stage j+4 (plane z) and T stage j
-    int s8 = 8 % SP, ph8 = (8 / SP) & 1;
-    int s4 = 4 % SP;
-    int st = 0, pht = 0;
+    int sn = 4 % SP, phn = (4 / SP) & 1;   // P stage i+4
+    int sx = 2 % SP;                        // P stage i+2
+    int st = 0, pht = 0;                    // T stage i
 
-    auto body = [&](int j, auto rot) {
-        constexpr int R = decltype(rot)::value;
-        // fast path: both stages already landed; else bounded waits
-        if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[s8], ph8) & mbar_try_wait(&fullT[st], pht))) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&fullP[s8], ph8, &s_abort) &&
-                                             mbar_wait(&fullT[st], pht, &s_abort));
-            if (!ok)
-                return;
-        }
-        const int z = z0 + j;
-        const float azv = azn;
-        if (prm.has_sponge && z + 1 < z1)
-            azn = prm.az[z + 1];
-        Q[8 + R] = *reinterpret_cast<const float4 *>(sP + s8 * PBOX + cP);
-        const float *pl = sP + s4 * PBOX + cP;
+    // Output plane z0+j from its P plane pl (centre float4), Pold/w tile tb and az;
+    // L'P in packed FP32 in the same rounding order as update_point<3>.
+    auto plane = [&](int j, const float *pl, const float *tb, float azv, auto qo) {
+        constexpr int O = decltype(qo)::value;   // Q index of this plane's centre
         const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
         const float4 xc = *reinterpret_cast<const float4 *>(pl);
         const float4 xp = *reinterpret_cast<const float4 *>(pl + 4);
@@ -210,13 +208,10 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
             ym[k - 1] = *reinterpret_cast<const float4 *>(pl - k * HX);
             yp[k - 1] = *reinterpret_cast<const float4 *>(pl + k * HX);
         }
-        const float4 old = *reinterpret_cast<const float4 *>(sT + (2 * st) * TBOX + cT);
-        const float4 wv = *reinterpret_cast<const float4 *>(sT + (2 * st + 1) * TBOX + cT);
+        const float4 old = *reinterpret_cast<const float4 *>(tb);
+        const float4 wv = *reinterpret_cast<const float4 *>(tb + 2 * TBOX);
         const float xa[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
-        const float4 &pc = Q[4 + R];
-
-        // L'P for the points (0,1) and (2,3) with packed FP32 arithmetic, in the
-        // same rounding order as update_point<3>
+        const float4 &pc = Q[O];
         float2 acc[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -224,16 +219,15 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
             float2 a2;
 #pragma unroll
             for (int k = 1; k <= 4; ++k) {
-                const float2 sx = xpair2(xa, h, k);
+                const float2 sxx = xpair2(xa, h, k);
                 const float2 sy = __fadd2_rn(half2of(yp[k - 1], h), half2of(ym[k - 1], h));
-                const float2 sz = __fadd2_rn(half2of(Q[4 + k + R], h), half2of(Q[4 - k + R], h));
-                const float2 d = __ffma2_rn(M2, p2, __fadd2_rn(__fadd2_rn(sx, sy), sz));
+                const float2 sz = __fadd2_rn(half2of(Q[O + k], h), half2of(Q[O - k], h));
+                const float2 d = __ffma2_rn(M2, p2, __fadd2_rn(__fadd2_rn(sxx, sy), sz));
                 const float2 ck = k == 1 ? C1 : k == 2 ? C2 : k == 3 ? C3 : C4;
                 a2 = k == 1 ? __fmul2_rn(ck, d) : __ffma2_rn(ck, d, a2);
             }
             acc[h] = a2;
         }
-
         const float ayz = ayv + azv;
         float2 r[2];
         if (x_band || ayz != 0.f) {
@@ -256,13 +250,8 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
                 r[h] = __ffma2_rn(half2of(wv, h), acc[h], t);
             }
         }
-        if (src_col && z == prm.sz) {
-            const int e = prm.sx - x;
-            if (e == 0) r[0].x += prm.src_amp;
-            if (e == 1) r[0].y += prm.src_amp;
-            if (e == 2) r[1].x += prm.src_amp;
-            if (e == 3) r[1].y += prm.src_amp;
-        }
+        if (src_col && z0 + j == prm.sz)
+            add_source4(r, prm.sx - x, prm.src_amp);
         float *dst = out_col + (size_t)j * plane_stride;
         if (store_vec) {
             *reinterpret_cast<float4 *>(dst) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
@@ -271,35 +260,60 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
             if (x + 1 < prm.nx) dst[1] = r[0].y;
             if (x + 2 < prm.nx) dst[2] = r[1].x;
         }
-        release(j + 4, s4, j, st);
-        if (++s8 == SP) {
-            s8 = 0;
-            ph8 ^= 1;
+    };
+
+    auto body = [&](int i, auto rot) {
+        constexpr int R = decltype(rot)::value;
+        // fast path: both stages already landed; else bounded waits
+        if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[sn], phn) & mbar_try_wait(&fullT[st], pht))) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&fullP[sn], phn, &s_abort) &&
+                                             mbar_wait(&fullT[st], pht, &s_abort));
+            if (!ok)
+                return;
         }
-        if (++s4 == SP)
-            s4 = 0;
+        const int j = 2 * i;
+        const float a0v = az0, a1v = az1;
+        if (prm.has_sponge) {
+            az0 = prm.az[z0 + j + 2];
+            az1 = prm.az[z0 + j + 3];
+        }
+        const float *pn = sP + sn * PST + cP;
+        Q[8 + 2 * R] = *reinterpret_cast<const float4 *>(pn);
+        Q[9 + 2 * R] = *reinterpret_cast<const float4 *>(pn + PBOX);
+        const float *pl = sP + sx * PST + cP;
+        const float *tb = sT + st * TST + cT;
+        plane(j, pl, tb, a0v, std::integral_constant<int, 4 + 2 * R>{});
+        if (j + 1 < nb)
+            plane(j + 1, pl + PBOX, tb + TBOX, a1v, std::integral_constant<int, 5 + 2 * R>{});
+        release(i + 2, sx, i, st);
+        if (++sn == SP) {
+            sn = 0;
+            phn ^= 1;
+        }
+        if (++sx == SP)
+            sx = 0;
         if (++st == ST) {
             st = 0;
             pht ^= 1;
         }
     };
 
-    for (int jb = 0; ok && jb < nb; jb += 3) {
-        body(jb, std::integral_constant<int, 0>{});
-        if (ok && jb + 1 < nb)
-            body(jb + 1, std::integral_constant<int, 1>{});
-        if (ok && jb + 2 < nb)
-            body(jb + 2, std::integral_constant<int, 2>{});
+    for (int ib = 0; ok && ib < nbh; ib += G) {
+        body(ib, std::integral_constant<int, 0>{});
+        if constexpr (G > 1) {
+            if (ok && ib + 1 < nbh)
+                body(ib + 1, std::integral_constant<int, 1>{});
+        }
+        if constexpr (G > 2) {
+            if (ok && ib + 2 < nbh)
+                body(ib + 2, std::integral_constant<int, 2>{});
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-            Q[k] = Q[k + 3];
+            Q[k] = Q[k + 2 * G];
     }
-    if (ok) {
-        for (int k = nb + 4; k < nb + 8; ++k)
-            release(k, k % SP, -1, 0);
-    } else {
+    if (!ok)
         raise_error(prm.err, &s_abort, kDevErrTimeout);
-    }
     // After an abort, do not leave while copies into this CTA's shared memory may
     // be in flight: wait (bounded) for the newest use of every slot.
     __syncthreads();
@@ -425,13 +439,13 @@ __global__ void compute_w_kernel(const float *v, float *w, int nx, size_t rows, 
 
 // ------------------------------------------------------------------------ launchers
 
-#define FD_STEP3D step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3>
+#define FD_STEP3D step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3>
 
 size_t step3d_smem_bytes()
 {
     constexpr int PBOX = (kTX3 + 8) * (kTY3 + 8);
     constexpr int TBOX = kTX3 * kTY3;
-    return (size_t)(kStagesP3 * PBOX + kStagesT3 * 2 * TBOX) * sizeof(float) +
+    return (size_t)(kStagesP3 * kPlanes3 * PBOX + kStagesT3 * kPlanes3 * 2 * TBOX) * sizeof(float) +
            (kStagesP3 + kStagesT3) * (sizeof(uint64_t) + sizeof(unsigned));
 }
 
