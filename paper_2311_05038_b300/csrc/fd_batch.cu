@@ -94,6 +94,12 @@ struct StageMeta {
     int cs;                // the step this stage computes (run-relative)
 };
 
+// A stage's receiver row, handed from before the stage barrier to after it.
+struct GatherRow {
+    float *row;            // trace row, or null
+    int begin, end;        // receiver range of the item
+};
+
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
     int v;
@@ -126,11 +132,6 @@ __device__ __forceinline__ bool named_and(int id, int nthreads, bool v)
         : "r"((int)v), "r"(id), "r"(nthreads)
         : "memory");
     return r != 0;
-}
-
-__device__ __forceinline__ void named_sync(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed(const int *p)
@@ -186,11 +187,12 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
     float *sW = sO + S * TBOX;
     float *sAx = sW + S * TBOX;             // [S][TX] sponge slice along x
     float *sAz = sAx + S * TX;              // [S][TZ] sponge slice along z
-    float *sPn = sAz + S * TZ;              // [TBOX] results, for the receivers
-    uint64_t *full = reinterpret_cast<uint64_t *>(sPn + TBOX);
+    float *sPn = sAz + S * TZ;              // [2][TBOX] results, for the receivers
+    uint64_t *full = reinterpret_cast<uint64_t *>(sPn + 2 * TBOX);
     uint64_t *empty = full + S;
     StageMeta *meta = reinterpret_cast<StageMeta *>(empty + S);
     __shared__ int s_abort;
+    __shared__ GatherRow s_gather[2];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -283,53 +285,64 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
         }
     } else {
         // ------------------------------------------------------------ consumers
+        // One named barrier per stage, which also votes: every consumer thread
+        // reaches it, including a warp whose wait gave up (it skips the work), so
+        // all take the same decision to go on or stop and none is left waiting.
         const int tx = tid % QX;
         const int tz = tid / QX;
         for (int k = 0;; ++k) {
             const int slot = k % S;
-            // every consumer thread takes the same decision, so none is left
-            // waiting at the item's named barriers after the others gave up
-            if (!named_and(1, NC, mbar_wait(&full[slot], (k / S) & 1, &s_abort))) {
+            float *pn = sPn + (k & 1) * TBOX;
+            const bool good = __all_sync(0xffffffffu, mbar_wait(&full[slot], (k / S) & 1, &s_abort));
+            bool work = false;
+            if (good) {
+                const StageMeta &mt = meta[slot];
+                work = mt.item >= 0;
+                if (work) {
+                    const int x = mt.x0 + 4 * tx;
+                    const int z = mt.z0 + tz;
+                    float axv[4] = {0.f, 0.f, 0.f, 0.f};
+                    float azv = 0.f;
+                    if (mt.has_sponge) {
+                        const float4 a4 = *reinterpret_cast<const float4 *>(sAx + slot * TX + 4 * tx);
+                        axv[0] = a4.x;
+                        axv[1] = a4.y;
+                        axv[2] = a4.z;
+                        axv[3] = a4.w;
+                        azv = sAz[slot * TZ + tz];
+                    }
+                    float2 r[2];
+                    tile2d_update<TX>(sP + slot * PBOX, sO + slot * TBOX, sW + slot * TBOX, tx, tz, axv, azv, bp.c1,
+                                      bp.c2, bp.c3, bp.c4, r);
+                    const int local = tz * TX + 4 * tx;
+                    if ((unsigned)(mt.src_local - local) < 4u)
+                        add_source4(r, mt.src_local - local, mt.src_amp);
+                    if (z < mt.nz && x < mt.nx)
+                        store4(mt.out + (size_t)z * mt.px + x, r, mt.nx - x);
+                    if (mt.rec_begin < mt.rec_end)
+                        *reinterpret_cast<float4 *>(pn + local) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+                    if (tid == 0)
+                        s_gather[k & 1] = GatherRow{mt.trace_row, mt.rec_begin, mt.rec_end};
+                }
+            } else {
                 raise_error(bp.err, &s_abort, kDevErrTimeout);
-                break;
             }
-            const StageMeta &mt = meta[slot];
-            const int item = mt.item;
-            if (item < 0)
-                break;
-            const int x = mt.x0 + 4 * tx;
-            const int z = mt.z0 + tz;
-            float axv[4] = {0.f, 0.f, 0.f, 0.f};
-            float azv = 0.f;
-            if (mt.has_sponge) {
-                const float4 a4 = *reinterpret_cast<const float4 *>(sAx + slot * TX + 4 * tx);
-                axv[0] = a4.x;
-                axv[1] = a4.y;
-                axv[2] = a4.z;
-                axv[3] = a4.w;
-                azv = sAz[slot * TZ + tz];
-            }
-            float2 r[2];
-            tile2d_update<TX>(sP + slot * PBOX, sO + slot * TBOX, sW + slot * TBOX, tx, tz, axv, azv, bp.c1, bp.c2,
-                              bp.c3, bp.c4, r);
-            const int local = tz * TX + 4 * tx;
-            if ((unsigned)(mt.src_local - local) < 4u)
-                add_source4(r, mt.src_local - local, mt.src_amp);
-            if (z < mt.nz && x < mt.nx)
-                store4(mt.out + (size_t)z * mt.px + x, r, mt.nx - x);
-            if (mt.rec_begin < mt.rec_end) {
-                *reinterpret_cast<float4 *>(sPn + local) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
-                named_sync(1, NC);
-                if (mt.trace_row)
-                    for (int q = mt.rec_begin + tid; q < mt.rec_end; q += NC)
-                        mt.trace_row[bp.recs[q].r] = sPn[bp.recs[q].local];
-            }
-            named_sync(1, NC);
+            if (!named_and(1, NC, work))
+                break;   // end marker, or some consumer gave up
             if (tid == 0) {
+                // the slot is still this stage's until the empty arrive below
+                const int item = meta[slot].item, cs = meta[slot].cs;
                 __threadfence();
-                st_release(&bp.counters[item], mt.cs + 1);
+                st_release(&bp.counters[item], cs + 1);
                 mbar_arrive(&empty[slot]);
             }
+            // Receivers of this stage, from the double-buffered result tile and
+            // row record: stage k+1 writes the other ones, and stage k+2 passes
+            // stage k+1's barrier only when every thread has finished reading.
+            const GatherRow gr = s_gather[k & 1];
+            if (gr.row)
+                for (int q = gr.begin + tid; q < gr.end; q += NC)
+                    gr.row[bp.recs[q].r] = pn[bp.recs[q].local];
         }
     }
 
@@ -359,7 +372,7 @@ static Variant variant()
 {
     constexpr int PBOX = (TX + 8) * (TZ + 8);
     constexpr int TBOX = TX * TZ;
-    const size_t smem = (size_t)(kBatchStages * (PBOX + 2 * TBOX + TX + TZ) + TBOX) * 4 + 2 * kBatchStages * 8 +
+    const size_t smem = (size_t)(kBatchStages * (PBOX + 2 * TBOX + TX + TZ) + 2 * TBOX) * 4 + 2 * kBatchStages * 8 +
                         kBatchStages * sizeof(StageMeta);
     return Variant{TX, TZ, (const void *)batch2d_kernel<TX, TZ, kBatchStages>, TX / 4 * TZ + 32, smem};
 }
