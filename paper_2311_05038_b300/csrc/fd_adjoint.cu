@@ -42,29 +42,53 @@ __global__ void inject_kernel(float *P, const float *w, const float *ax, const f
 
 // grad[i] += psi[i] * (L'p)[i] over dense [nz][ny][nx] arrays p and grad; psi is pitched.
 // L'p = sum over the axes of sum_k c_k ((p[+k] + p[-k]) - 2 p), zero outside the grid.
-__global__ void __launch_bounds__(256) imaging_kernel(const float *__restrict__ psi, const float *__restrict__ p,
-                                                      float *__restrict__ grad, int nx, int ny, int nz, int px,
-                                                      int ndim, float c1, float c2, float c3, float c4)
+//
+// A block of 32 x kImgRows threads owns a 32-wide x segment of kImgRows rows
+// (y in 3D; in 2D the rows are further x segments) and marches along z through
+// kImgChunk planes; each thread keeps the 9 values p[z-4 .. z+4] of its own
+// column in registers, and reads its x and y neighbours through L1.
+constexpr int kImgRows = 8;
+constexpr int kImgChunk = 32;
+
+template <int NDIM>
+__global__ void __launch_bounds__(32 * kImgRows) imaging_kernel(const float *__restrict__ psi,
+                                                                const float *__restrict__ p,
+                                                                float *__restrict__ grad, int nx, int ny, int nz,
+                                                                int px, float c1, float c2, float c3, float c4)
 {
-    const long long n = (long long)nx * ny * nz;
+    const int x = NDIM == 3 ? blockIdx.x * 32 + threadIdx.x : (blockIdx.x * kImgRows + threadIdx.y) * 32 + threadIdx.x;
+    const int y = NDIM == 3 ? blockIdx.y * kImgRows + threadIdx.y : 0;
+    const int z0 = blockIdx.z * kImgChunk;
+    const int z1 = min(nz, z0 + kImgChunk);
+    if (x >= nx || y >= ny)
+        return;
+    const size_t plane = (size_t)nx * ny;
+    const float *col = p + (size_t)y * nx + x;   // p[z][y][x] = col[z * plane]
+    float q[9];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int z = z0 - 4 + i;
+        q[i] = (z >= 0 && z < nz) ? col[(size_t)z * plane] : 0.f;
+    }
     const float ck[4] = {c1, c2, c3, c4};
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx);
-        const long long row = i / nx;
-        const int y = (int)(row % ny);
-        const int z = (int)(row / ny);
-        const float pc = p[i];
+    for (int z = z0; z < z1; ++z) {
+        q[8] = z + 4 < nz ? col[(size_t)(z + 4) * plane] : 0.f;
+        const float *c = col + (size_t)z * plane;
+        const float pc = q[4];
         float lap = 0.f;
 #pragma unroll
         for (int k = 1; k <= 4; ++k) {
-            float s = (x + k < nx ? p[i + k] : 0.f) + (x - k >= 0 ? p[i - k] : 0.f);
-            s += (z + k < nz ? p[i + (long long)k * nx * ny] : 0.f) + (z - k >= 0 ? p[i - (long long)k * nx * ny] : 0.f);
-            if (ndim == 3)
-                s += (y + k < ny ? p[i + (long long)k * nx] : 0.f) + (y - k >= 0 ? p[i - (long long)k * nx] : 0.f);
-            lap = fmaf(ck[k - 1], fmaf(-2.0f * ndim, pc, s), lap);
+            float s = (x + k < nx ? c[k] : 0.f) + (x - k >= 0 ? c[-k] : 0.f);
+            s += q[4 + k] + q[4 - k];
+            if (NDIM == 3)
+                s += (y + k < ny ? c[(size_t)k * nx] : 0.f) + (y - k >= 0 ? c[-(ptrdiff_t)k * nx] : 0.f);
+            lap = fmaf(ck[k - 1], fmaf(-2.0f * NDIM, pc, s), lap);
         }
-        grad[i] = fmaf(psi[row * px + x], lap, grad[i]);
+        const size_t i = (size_t)z * plane + (size_t)y * nx + x;
+        grad[i] = fmaf(psi[((size_t)z * ny + y) * px + x], lap, grad[i]);
+#pragma unroll
+        for (int i2 = 0; i2 < 8; ++i2)
+            q[i2] = q[i2 + 1];
     }
 }
 
@@ -135,10 +159,18 @@ extern "C" fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_d
     FD_CUDA(cudaSetDevice(adj->device), "cudaSetDevice");
     float w4[4];
     fd_stencil_weights(w4);
-    const long long n = (long long)adj->npts;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
-    imaging_kernel<<<blocks, 256, 0, adj->stream>>>(adj->buf[adj->cur], p_dev, grad_dev, adj->nx, adj->ny, adj->nz,
-                                                    adj->px, adj->d.ndim, w4[0], w4[1], w4[2], w4[3]);
+    const int nx = adj->nx, ny = adj->ny, nz = adj->nz;
+    const dim3 block(32, kImgRows);
+    const unsigned gz = (unsigned)((nz + kImgChunk - 1) / kImgChunk);
+    if (adj->d.ndim == 3) {
+        const dim3 grid((nx + 31) / 32, (ny + kImgRows - 1) / kImgRows, gz);
+        imaging_kernel<3><<<grid, block, 0, adj->stream>>>(adj->buf[adj->cur], p_dev, grad_dev, nx, ny, nz, adj->px,
+                                                           w4[0], w4[1], w4[2], w4[3]);
+    } else {
+        const dim3 grid((nx + 32 * kImgRows - 1) / (32 * kImgRows), 1, gz);
+        imaging_kernel<2><<<grid, block, 0, adj->stream>>>(adj->buf[adj->cur], p_dev, grad_dev, nx, 1, nz, adj->px,
+                                                           w4[0], w4[1], w4[2], w4[3]);
+    }
     ++g_launches;
     FD_CUDA(cudaGetLastError(), "imaging launch");
     return FD_OK;
