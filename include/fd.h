@@ -186,6 +186,17 @@ fd_status fd_inject_receivers(fd_model *m, const float *values_dev);
 /* grad_dev += P_adj * (L' p_dev) over dense [nz][ny][nx] device arrays, where
  * P_adj is the current level of the model adj and L' the stencil sum. */
 fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_dev);
+/* One time step, as fd_step(m, 1), that also writes L'P^n -- the stencil sum of
+ * the level n it consumes, sum_k c_k D_k in the step's own FP32 arithmetic --
+ * to lp_dev, a dense [nz][ny][nx] device array (asynchronous).  This is the
+ * factor the imaging condition needs, produced while the forward segment is
+ * recomputed, so the adjoint pass needs neither a copy of P^n nor a second
+ * stencil. */
+fd_status fd_step_lp(fd_model *m, float *lp_dev);
+/* grad_dev += P_adj * lp_dev pointwise over dense [nz][ny][nx] device arrays,
+ * where P_adj is the current level of adj and lp_dev comes from fd_step_lp
+ * (asynchronous on adj's stream). */
+fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, float *grad_dev);
 
 /* --------------------------------------------------------- unfused routines
  *

@@ -10,14 +10,16 @@ wavefield psi obeys the same damped leapfrog backwards in time,
 
 so it advances with ``fd_step`` on a second model with the same velocity and no
 source, the receiver terms entering through ``fd_inject_receivers``; the
-gradient is dJ/dm = -(1/m) sum_n psi_{n+1} L'P^n, accumulated by ``fd_imaging``.
-The sponge's damping is held fixed.
+gradient is dJ/dm = -(1/m) sum_n psi_{n+1} L'P^n.  The sponge's damping is held
+fixed.
 
 Memory is bounded by checkpointing: the forward pass keeps (P, Pold) every
-``checkpoint_every`` steps; the backward pass walks the segments last to first,
-recomputes each segment's forward levels from its checkpoint into a buffer of
-``checkpoint_every`` fields, and runs the adjoint through it.  The forward
-work is therefore done twice.
+``checkpoint_every`` steps; the backward pass walks the segments last to first
+and recomputes each segment from its checkpoint with ``fd_step_lp``, which
+stores the stencil sums L'P^n the imaging condition needs (one field per step
+of the segment) instead of the levels themselves.  The adjoint then runs through
+the segment, and ``fd_imaging_product`` adds psi_{n+1} L'P^n pointwise.  The
+forward work is therefore done twice, and no stencil is evaluated a third time.
 """
 from __future__ import annotations
 
@@ -119,14 +121,12 @@ def _make_function():
                 n1 = min(n0 + K, geo.nt)
                 P, Po = ctx.ckpts[s]
                 fd.fd_set_wavefield_dev(model.handle, P, Po, n0)
-                seg[0].copy_(P)
-                for j in range(1, n1 - n0):
-                    fd.fd_step(model.handle, 1)
-                    fd.fd_get_wavefield_dev(model.handle, seg[j])
+                for j in range(n1 - n0):
+                    fd.fd_step_lp(model.handle, seg[j])             # seg[j] = L'P^{n0+j}
                 for k in range(n1, n0, -1):
                     fd.fd_step(adj.handle, 1)                     # psi_k from psi_{k+1}, psi_{k+2}
                     fd.fd_inject_receivers(adj.handle, g[k - 1])  # + w g^{k-1} / (1 + a)
-                    fd.fd_imaging(adj.handle, seg[k - 1 - n0], acc)
+                    fd.fd_imaging_product(adj.handle, seg[k - 1 - n0], acc)
             fd.fd_synchronize(adj.handle)
             adj.close()
             model.close()

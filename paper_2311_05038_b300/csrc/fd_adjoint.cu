@@ -92,6 +92,21 @@ __global__ void __launch_bounds__(32 * kImgRows) imaging_kernel(const float *__r
     }
 }
 
+// grad[i] += psi[i] * lp[i] with lp = L'P^n as written by fd_step_lp: dense
+// grad and lp, pitched psi.  One block per group of rows, threads along x.
+__global__ void __launch_bounds__(256) imaging_product_kernel(const float *__restrict__ psi,
+                                                              const float *__restrict__ lp,
+                                                              float *__restrict__ grad, int nx, size_t rows, int px)
+{
+    for (size_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const float *ps = psi + row * px;
+        const float *l = lp + row * nx;
+        float *g = grad + row * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x)
+            g[x] = fmaf(ps[x], l[x], g[x]);
+    }
+}
+
 }  // namespace fdk
 
 using namespace fdk;
@@ -173,5 +188,18 @@ extern "C" fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_d
     }
     ++g_launches;
     FD_CUDA(cudaGetLastError(), "imaging launch");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, float *grad_dev)
+{
+    if (!adj || !lp_dev || !grad_dev)
+        return fail(FD_EINVAL, "fd_imaging_product: NULL argument");
+    FD_CUDA(cudaSetDevice(adj->device), "cudaSetDevice");
+    const int blocks = (int)std::min<size_t>(adj->rows, 148 * 64);
+    imaging_product_kernel<<<blocks, 256, 0, adj->stream>>>(adj->buf[adj->cur], lp_dev, grad_dev, adj->nx, adj->rows,
+                                                            adj->px);
+    ++g_launches;
+    FD_CUDA(cudaGetLastError(), "imaging product launch");
     return FD_OK;
 }

@@ -594,12 +594,12 @@ static fd_status flush_pending(fd_model *m)
     return FD_OK;
 }
 
-extern "C" fd_status fd_step(fd_model *m, int nsteps)
+// nsteps time steps; if lp is set (nsteps == 1), the step also writes L'P of the
+// level it consumes to lp (dense [nz][ny][nx]).
+static fd_status step_n(fd_model *m, int nsteps, float *lp)
 {
-    NEED_MODEL(m);
-    if (nsteps < 0)
-        return fail(FD_EINVAL, "nsteps must be >= 0");
     StepParams p{};
+    p.lp_out = lp;
     float w4[4];
     fd_stencil_weights(w4);
     p.c1 = w4[0];
@@ -639,6 +639,22 @@ extern "C" fd_status fd_step(fd_model *m, int nsteps)
         ++m->n;
     }
     return flush_pending(m);
+}
+
+extern "C" fd_status fd_step(fd_model *m, int nsteps)
+{
+    NEED_MODEL(m);
+    if (nsteps < 0)
+        return fail(FD_EINVAL, "nsteps must be >= 0");
+    return step_n(m, nsteps, nullptr);
+}
+
+extern "C" fd_status fd_step_lp(fd_model *m, float *lp_dev)
+{
+    NEED_MODEL(m);
+    if (!lp_dev)
+        return fail(FD_EINVAL, "fd_step_lp: NULL output");
+    return step_n(m, 1, lp_dev);
 }
 
 extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)

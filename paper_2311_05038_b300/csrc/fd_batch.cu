@@ -311,9 +311,9 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
                         axv[3] = a4.w;
                         azv = sAz[slot * TZ + tz];
                     }
-                    float2 r[2];
+                    float2 r[2], lp[2];
                     tile2d_update<TX>(sP + slot * PBOX, sO + slot * TBOX, sW + slot * TBOX, tx, tz, axv, azv, bp.c1,
-                                      bp.c2, bp.c3, bp.c4, r);
+                                      bp.c2, bp.c3, bp.c4, r, lp);
                     const int local = tz * TX + 4 * tx;
                     if ((unsigned)(mt.src_local - local) < 4u)
                         add_source4(r, mt.src_local - local, mt.src_amp);

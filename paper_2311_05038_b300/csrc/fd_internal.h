@@ -68,12 +68,14 @@ struct StepParams {
     const int64_t *rec_idx;   // receivers' pitched linear indices
     int nrec;
     float *trace_prev;        // if set: trace_prev[r] = P[rec_idx[r]] (previous step's row)
+    float *lp_out;            // if set (the *_lp launches): L'P of level n, dense [nz][ny][nx]
     int *err;                 // device error word
 };
 
 size_t step3d_smem_bytes();
 cudaError_t step3d_prepare();
 int step3d_blocks_per_sm();
+// With p.lp_out set, the launch also writes the stencil sum L'P of level n.
 cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
                           const StepParams &p, int nchunks, cudaStream_t s);
 cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,

@@ -48,7 +48,10 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 // free a slot, and that warp issues the slot's next stage at once, so loads run
 // ahead of the slowest warp without anyone blocking.  The only waits are the
 // bounded waits on the full barriers.
-template <int TX, int TY, int SP, int ST, int G>
+//
+// With LP set the kernel also writes L'P (the stencil sum of level n) to the
+// dense array prm.lp_out, for the adjoint's imaging condition.
+template <int TX, int TY, int SP, int ST, int G, bool LP>
 __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -250,6 +253,11 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
                 r[h] = __ffma2_rn(half2of(wv, h), acc[h], t);
             }
         }
+        if constexpr (LP) {
+            if (store_any)
+                store4_dense(prm.lp_out + ((size_t)(z0 + j) * prm.ny + y) * prm.nx + x, acc, prm.nx - x,
+                             (prm.nx & 3) == 0);
+        }
         if (src_col && z0 + j == prm.sz)
             add_source4(r, prm.sx - x, prm.src_amp);
         float *dst = out_col + (size_t)j * plane_stride;
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
 // A CTA owns one TX x TZ tile of the [nz][nx] grid.  One TMA transaction brings
 // the haloed P tile and the Pold and w tiles; each thread computes 4
 // consecutive x points of one row.
-template <int TX, int TZ>
+template <int TX, int TZ, bool LP>
 __global__ void __launch_bounds__(TX / 4 * TZ)
     step2d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -383,12 +391,15 @@ __global__ void __launch_bounds__(TX / 4 * TZ)
             raise_error(prm.err, &s_abort, kDevErrTimeout);
         return;
     }
-    float2 r[2];
-    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r);
+    float2 r[2], lp[2];
+    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
     if (prm.src_on && z == prm.sz && (unsigned)(prm.sx - x) < 4u)
         add_source4(r, prm.sx - x, prm.src_amp);
-    if (z < prm.nz && x < prm.nx)
+    if (z < prm.nz && x < prm.nx) {
         store4(prm.out + (size_t)z * prm.px + x, r, prm.nx - x);
+        if constexpr (LP)
+            store4_dense(prm.lp_out + (size_t)z * prm.nx + x, lp, prm.nx - x, (prm.nx & 3) == 0);
+    }
 }
 
 // ------------------------------------------------------------------------ helpers
@@ -439,7 +450,7 @@ __global__ void compute_w_kernel(const float *v, float *w, int nx, size_t rows, 
 
 // ------------------------------------------------------------------------ launchers
 
-#define FD_STEP3D step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3>
+#define FD_STEP3D(LP) step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3, LP>
 
 size_t step3d_smem_bytes()
 {
@@ -451,13 +462,19 @@ size_t step3d_smem_bytes()
 
 cudaError_t step3d_prepare()
 {
-    return cudaFuncSetAttribute(FD_STEP3D, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(FD_STEP3D(false), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step3d_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)step3d_smem_bytes());
+    return e;
 }
 
 int step3d_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FD_STEP3D, kThreads3, step3d_smem_bytes()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FD_STEP3D(false), kThreads3, step3d_smem_bytes()) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -467,7 +484,10 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
 {
     const int tiles = ((p.nx + kTX3 - 1) / kTX3) * ((p.ny + kTY3 - 1) / kTY3);
     dim3 grid(tiles, nchunks);
-    FD_STEP3D<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    if (p.lp_out)
+        FD_STEP3D(true)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else
+        FD_STEP3D(false)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
 }
 
@@ -475,7 +495,10 @@ cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
                           const StepParams &p, cudaStream_t s)
 {
     const int tiles = ((p.nx + kTX2 - 1) / kTX2) * ((p.nz + kTZ2 - 1) / kTZ2);
-    step2d_kernel<kTX2, kTZ2><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    if (p.lp_out)
+        step2d_kernel<kTX2, kTZ2, true><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    else
+        step2d_kernel<kTX2, kTZ2, false><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
 }
 

@@ -62,11 +62,12 @@ __device__ __forceinline__ void raise_error(int *err, volatile int *abort_flag, 
 // One thread's 4 consecutive x points of a 2D tile held in shared memory: P
 // box (TX+8) x (TZ+8) with a 4-point halo, Pold and w tiles TX x TZ.  Packed
 // FP32 arithmetic in the rounding order of update_point<2>; sponge points use
-// __fdividef.  Returns the new values in r[0] (points 0, 1) and r[1] (2, 3).
+// __fdividef.  Returns the new values in r[0] (points 0, 1) and r[1] (2, 3),
+// and the stencil sums L'P of the same points in lp.
 template <int TX>
 __device__ __forceinline__ void tile2d_update(const float *sP, const float *sO, const float *sW, int tx, int tz,
                                               const float (&axv)[4], float azv, float c1, float c2, float c3,
-                                              float c4, float2 (&r)[2])
+                                              float c4, float2 (&r)[2], float2 (&lp)[2])
 {
     constexpr int HX = TX + 8;
     const float *pl = sP + (tz + 4) * HX + 4 * tx + 4;
@@ -98,6 +99,7 @@ __device__ __forceinline__ void tile2d_update(const float *sP, const float *sO, 
             a2 = k == 1 ? __fmul2_rn(make_float2(ck, ck), d) : __ffma2_rn(make_float2(ck, ck), d, a2);
         }
         acc[h] = a2;
+        lp[h] = a2;
     }
     if (axv[0] != 0.f || axv[1] != 0.f || axv[2] != 0.f || axv[3] != 0.f || azv != 0.f) {
 #pragma unroll
@@ -126,6 +128,20 @@ __device__ __forceinline__ void add_source4(float2 (&r)[2], int e, float amp)
     if (e == 1) r[0].y += amp;
     if (e == 2) r[1].x += amp;
     if (e == 3) r[1].y += amp;
+}
+
+// Store 4 consecutive points of a dense row at dst (any alignment), of which the
+// first is inside the row and `valid` are.
+__device__ __forceinline__ void store4_dense(float *dst, const float2 (&v)[2], int valid, bool aligned)
+{
+    if (aligned && valid >= 4) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    } else {
+        dst[0] = v[0].x;
+        if (valid > 1) dst[1] = v[0].y;
+        if (valid > 2) dst[2] = v[1].x;
+        if (valid > 3) dst[3] = v[1].y;
+    }
 }
 
 // Store 4 consecutive points, of which the first is known to be inside the row.

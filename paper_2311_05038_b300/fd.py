@@ -40,7 +40,7 @@ EXPORTS = [
     "fd_batch_create", "fd_batch_destroy", "fd_batch_set_tuning", "fd_batch_get_tuning", "fd_batch_step",
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
-    "fd_set_sponge_vmax", "fd_batch_set_fault",
+    "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
 ]
 
 
@@ -108,6 +108,8 @@ _SIGS = {
     "fd_set_wavefield_dev": (_i, [_vp, _vp, _vp, _i]),
     "fd_inject_receivers": (_i, [_vp, _vp]),
     "fd_imaging": (_i, [_vp, _vp, _vp]),
+    "fd_step_lp": (_i, [_vp, _vp]),
+    "fd_imaging_product": (_i, [_vp, _vp, _vp]),
     "fd_set_sponge_vmax": (_i, [_vp, ctypes.c_double]),
     "fd_batch_set_fault": (_i, [_vp, _i]),
     "fd_step_unfused": (_i, [_vp, _i]),
@@ -368,6 +370,16 @@ def fd_inject_receivers(m: int, values_dev):
 
 def fd_imaging(adj: int, p_dev, grad_dev):
     _check(_lib.fd_imaging(adj, _dev_ptr(p_dev), _dev_ptr(grad_dev)), "fd_imaging")
+
+
+def fd_step_lp(m: int, lp_dev):
+    """One step that also writes L'P of the consumed level to lp_dev (dense, grid-shaped)."""
+    _check(_lib.fd_step_lp(m, _dev_ptr(lp_dev)), "fd_step_lp")
+
+
+def fd_imaging_product(adj: int, lp_dev, grad_dev):
+    """grad_dev += (adj's current level) * lp_dev, pointwise."""
+    _check(_lib.fd_imaging_product(adj, _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_imaging_product")
 
 
 # ------------------------------------------------------------------ convenience

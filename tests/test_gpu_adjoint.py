@@ -111,3 +111,51 @@ def test_gradient_independent_of_checkpoint_interval(fdlib):
         grads.append(adjoint.misfit_and_gradient(m, geo, dobs)[1].cpu().numpy())
     np.testing.assert_array_equal(grads[0], grads[1])
     np.testing.assert_array_equal(grads[0], grads[2])
+
+
+def _random_shot(shape, seed):
+    rng = np.random.default_rng(seed)
+    vel = rng.uniform(1500, 2500, shape).astype(np.float32)
+    ndim = len(shape)
+    dt = 0.4 * 10.0 / 2500.0
+    src = tuple(int(rng.integers(0, n)) for n in reversed(shape)) if ndim == 3 else \
+        (int(rng.integers(0, shape[1])), 0, int(rng.integers(0, shape[0])))
+    nt = 4
+    return wl.Shot(ndim, shape, 10.0, dt, nt, vel, src, wl.ricker(nt, dt, 30.0), np.zeros((0, 3), np.int32),
+                   sponge_width=3)
+
+
+@pytest.mark.parametrize("shape", [(36, 32, 40), (21, 17, 29), (45, 38, 70), (60, 72), (33, 45)])
+def test_step_lp_writes_the_stencil_sum(fdlib, oracle, shape):
+    """fd_step_lp advances exactly as fd_step (bitwise) and writes L'P of the level it
+    consumed at every point, dense; nx = 29 and 45 take the unaligned store path, and
+    nz = 21, 33, 45 leave an odd plane count in a 3D chunk."""
+    import torch
+    shot = _random_shot(shape, seed=sum(shape))
+    P0, Pm1 = wl.random_state(shape, seed=len(shape) * 100 + shape[-1])
+    with fdlib.Model.from_shot(shot) as a, fdlib.Model.from_shot(shot) as b:
+        for m in (a, b):
+            fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
+        lp = torch.full(shape, float("nan"), device="cuda")
+        fdlib.fd_step_lp(a.handle, lp)
+        fdlib.fd_step(b.handle, 1)
+        np.testing.assert_array_equal(a.wavefield(), b.wavefield())
+        got = lp.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert pl.rel_l2(got, oracle.stencil_sum(P0)) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(21, 17, 29), (33, 45)])
+def test_imaging_product(fdlib, shape):
+    """grad += psi * lp pointwise, psi the adjoint model's current level."""
+    import torch
+    shot = _random_shot(shape, seed=7)
+    psi, lp = wl.random_state(shape, seed=11)
+    g0 = np.random.default_rng(12).standard_normal(shape).astype(np.float32)
+    with fdlib.Model.from_shot(shot) as adj:
+        fdlib.fd_set_wavefield(adj.handle, psi, np.zeros(shape, np.float32), 0)
+        grad = torch.from_numpy(g0).cuda()
+        fdlib.fd_imaging_product(adj.handle, torch.from_numpy(lp).cuda(), grad)
+        got = grad.cpu().numpy()
+    want = g0.astype(np.float64) + psi.astype(np.float64) * lp.astype(np.float64)
+    assert np.max(np.abs(got - want) / (np.abs(want) + 1e-3)) <= 1e-6
