@@ -197,6 +197,17 @@ fd_status fd_step_lp(fd_model *m, float *lp_dev);
  * where P_adj is the current level of adj and lp_dev comes from fd_step_lp
  * (asynchronous on adj's stream). */
 fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, float *grad_dev);
+/* One checkpoint segment [n0, n1) of the reverse-time adjoint, issued from the
+ * host in one call (asynchronous; fwd and adj must share a stream and a grid).
+ * The forward model fwd must be at step n0 (its levels n0 and n0-1 restored,
+ * e.g. by fd_set_wavefield_dev); it advances n1 - n0 steps with fd_step_lp,
+ * storing L'P^{n0+j} in lp_buf + j * nx*ny*nz (n1 - n0 dense fields, owned by
+ * the caller).  Then for k = n1 down to n0 + 1 the adjoint model adj takes one
+ * step, receives g_dev + (k-1) * nrec at its receivers (fd_inject_receivers)
+ * and adds psi_k * L'P^{k-1} to grad_dev (fd_imaging_product).  Returns
+ * FD_EINVAL for bad arguments, FD_ESTATE if fwd is not at step n0. */
+fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, int n1, float *lp_buf, const float *g_dev,
+                             float *grad_dev);
 
 /* --------------------------------------------------------- unfused routines
  *

@@ -18,7 +18,8 @@ Memory is bounded by checkpointing: the forward pass keeps (P, Pold) every
 and recomputes each segment from its checkpoint with ``fd_step_lp``, which
 stores the stencil sums L'P^n the imaging condition needs (one field per step
 of the segment) instead of the levels themselves.  The adjoint then runs through
-the segment, and ``fd_imaging_product`` adds psi_{n+1} L'P^n pointwise.  The
+the segment, and ``fd_imaging_product`` adds psi_{n+1} L'P^n pointwise; one
+``fd_adjoint_segment`` call issues a whole segment from native code.  The
 forward work is therefore done twice, and no stencil is evaluated a third time.
 """
 from __future__ import annotations
@@ -121,12 +122,9 @@ def _make_function():
                 n1 = min(n0 + K, geo.nt)
                 P, Po = ctx.ckpts[s]
                 fd.fd_set_wavefield_dev(model.handle, P, Po, n0)
-                for j in range(n1 - n0):
-                    fd.fd_step_lp(model.handle, seg[j])             # seg[j] = L'P^{n0+j}
-                for k in range(n1, n0, -1):
-                    fd.fd_step(adj.handle, 1)                     # psi_k from psi_{k+1}, psi_{k+2}
-                    fd.fd_inject_receivers(adj.handle, g[k - 1])  # + w g^{k-1} / (1 + a)
-                    fd.fd_imaging_product(adj.handle, seg[k - 1 - n0], acc)
+                # seg[j] = L'P^{n0+j}; then for k = n1 .. n0+1: psi_k from psi_{k+1},
+                # psi_{k+2}, + w g^{k-1} / (1 + a) at the receivers, acc += psi_k L'P^{k-1}
+                fd.fd_adjoint_segment(model.handle, adj.handle, n0, n1, seg, g, acc)
             fd.fd_synchronize(adj.handle)
             adj.close()
             model.close()

@@ -203,3 +203,31 @@ extern "C" fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, floa
     FD_CUDA(cudaGetLastError(), "imaging product launch");
     return FD_OK;
 }
+
+extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, int n1, float *lp_buf,
+                                        const float *g_dev, float *grad_dev)
+{
+    if (!fwd || !adj || !lp_buf || !grad_dev || (adj->nrec > 0 && !g_dev))
+        return fail(FD_EINVAL, "fd_adjoint_segment: NULL argument");
+    if (n0 < 0 || n1 <= n0)
+        return fail(FD_EINVAL, "fd_adjoint_segment: need 0 <= n0 < n1 (got %d, %d)", n0, n1);
+    if (fwd->nx != adj->nx || fwd->ny != adj->ny || fwd->nz != adj->nz || fwd->d.ndim != adj->d.ndim)
+        return fail(FD_EINVAL, "fd_adjoint_segment: models of different grids");
+    if (fwd->stream != adj->stream)
+        return fail(FD_EINVAL, "fd_adjoint_segment: the two models must share a stream");
+    if (fwd->n != n0)
+        return fail(FD_ESTATE, "fd_adjoint_segment: forward model at step %d, segment starts at %d", fwd->n, n0);
+    const size_t npts = (size_t)fwd->nx * fwd->ny * fwd->nz;
+    for (int j = 0; j < n1 - n0; ++j)
+        if (fd_status st = fd_step_lp(fwd, lp_buf + (size_t)j * npts))
+            return st;
+    for (int k = n1; k > n0; --k) {
+        if (fd_status st = fd_step(adj, 1))
+            return st;
+        if (fd_status st = fd_inject_receivers(adj, adj->nrec > 0 ? g_dev + (size_t)(k - 1) * adj->nrec : nullptr))
+            return st;
+        if (fd_status st = fd_imaging_product(adj, lp_buf + (size_t)(k - 1 - n0) * npts, grad_dev))
+            return st;
+    }
+    return FD_OK;
+}

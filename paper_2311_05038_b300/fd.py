@@ -41,6 +41,7 @@ EXPORTS = [
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
+    "fd_adjoint_segment",
 ]
 
 
@@ -110,6 +111,7 @@ _SIGS = {
     "fd_imaging": (_i, [_vp, _vp, _vp]),
     "fd_step_lp": (_i, [_vp, _vp]),
     "fd_imaging_product": (_i, [_vp, _vp, _vp]),
+    "fd_adjoint_segment": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
     "fd_set_sponge_vmax": (_i, [_vp, ctypes.c_double]),
     "fd_batch_set_fault": (_i, [_vp, _i]),
     "fd_step_unfused": (_i, [_vp, _i]),
@@ -380,6 +382,13 @@ def fd_step_lp(m: int, lp_dev):
 def fd_imaging_product(adj: int, lp_dev, grad_dev):
     """grad_dev += (adj's current level) * lp_dev, pointwise."""
     _check(_lib.fd_imaging_product(adj, _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_imaging_product")
+
+
+def fd_adjoint_segment(fwd: int, adj: int, n0: int, n1: int, lp_buf, g_dev, grad_dev):
+    """Recompute [n0, n1) with fd_step_lp into lp_buf, then run the adjoint back through it."""
+    _check(_lib.fd_adjoint_segment(fwd, adj, int(n0), int(n1), _dev_ptr(lp_buf),
+                                   None if g_dev is None else _dev_ptr(g_dev), _dev_ptr(grad_dev)),
+           "fd_adjoint_segment")
 
 
 # ------------------------------------------------------------------ convenience

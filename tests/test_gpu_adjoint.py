@@ -159,3 +159,63 @@ def test_imaging_product(fdlib, shape):
         got = grad.cpu().numpy()
     want = g0.astype(np.float64) + psi.astype(np.float64) * lp.astype(np.float64)
     assert np.max(np.abs(got - want) / (np.abs(want) + 1e-3)) <= 1e-6
+
+
+def _segment_case(fdlib, shape, seed):
+    shot = _random_shot(shape, seed)
+    rng = np.random.default_rng(seed)
+    ndim = len(shape)
+    rec = np.array([(int(rng.integers(0, shape[-1])), int(rng.integers(0, shape[1])) if ndim == 3 else 0,
+                     int(rng.integers(0, shape[0]))) for _ in range(9)], np.int32)
+    shot.receivers = rec
+    return shot
+
+
+@pytest.mark.parametrize("shape", [(21, 17, 29), (33, 45)])
+def test_adjoint_segment_equals_step_by_step_calls(fdlib, shape):
+    """fd_adjoint_segment issues exactly fd_step_lp x (n1-n0), then per k fd_step,
+    fd_inject_receivers and fd_imaging_product: results bitwise equal."""
+    import torch
+    shot = _segment_case(fdlib, shape, seed=5)
+    n0, n1 = 3, 9
+    P, Po = wl.random_state(shape, seed=21)
+    psi, psio = wl.random_state(shape, seed=22, scale=1e-3)
+    g = torch.from_numpy(np.random.default_rng(23).standard_normal((n1, len(shot.receivers))).astype(np.float32)).cuda()
+    out = []
+    for native in (True, False):
+        with fdlib.Model.from_shot(shot) as fwd, fdlib.Model.from_shot(shot) as adj:
+            fdlib.fd_set_wavefield(fwd.handle, P, Po, n0)
+            fdlib.fd_set_wavefield(adj.handle, psi, psio, 0)
+            lp = torch.zeros((n1 - n0,) + shape, device="cuda")
+            grad = torch.zeros(shape, device="cuda")
+            if native:
+                fdlib.fd_adjoint_segment(fwd.handle, adj.handle, n0, n1, lp, g, grad)
+            else:
+                for j in range(n1 - n0):
+                    fdlib.fd_step_lp(fwd.handle, lp[j])
+                for k in range(n1, n0, -1):
+                    fdlib.fd_step(adj.handle, 1)
+                    fdlib.fd_inject_receivers(adj.handle, g[k - 1])
+                    fdlib.fd_imaging_product(adj.handle, lp[k - 1 - n0], grad)
+            torch.cuda.synchronize()
+            out.append((lp.cpu().numpy(), grad.cpu().numpy(), adj.wavefield()))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(out[0][1]).max() > 0
+
+
+def test_adjoint_segment_argument_checks(fdlib):
+    import torch
+    shape = (21, 17, 29)
+    shot = _segment_case(fdlib, shape, seed=6)
+    g = torch.zeros((8, len(shot.receivers)), device="cuda")
+    lp = torch.zeros((4,) + shape, device="cuda")
+    grad = torch.zeros(shape, device="cuda")
+    with fdlib.Model.from_shot(shot) as fwd, fdlib.Model.from_shot(shot) as adj:
+        fdlib.fd_step(fwd.handle, 1)                      # forward model at step 1, not 0
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_adjoint_segment(fwd.handle, adj.handle, 0, 4, lp, g, grad)
+        assert e.value.status == -8                        # FD_ESTATE
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_adjoint_segment(fwd.handle, adj.handle, 1, 1, lp, g, grad)
+        assert e.value.status == -1                        # FD_EINVAL
