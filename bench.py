@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--skip-unfused", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
-    ap.add_argument("--adjoint-shots", type=int, default=2, help="adjoint workload: shots per gradient")
+    ap.add_argument("--adjoint-shots", type=int, default=8, help="adjoint workload: shots per gradient")
     ap.add_argument("--serve-shots", type=int, default=48, help="serving workload: requests in the stream")
     ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
@@ -380,6 +380,12 @@ def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
             m.run_shot(nt)
             observed.append(torch.from_numpy(m.traces(nt)).cuda())
     m0 = torch.from_numpy((1.0 / shots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    # untimed warm-up gradient on a small cut of the workload: loads the device code
+    # of every torch op on the path (casts, FP64 reduction, autograd) before timing
+    wshots, _ = wl.adjoint_3d(48, 40, 1)
+    wgeo = adjoint.Geometry.from_shot(wshots[0], checkpoint_every=10, sponge_vmax=vmax)
+    wm = torch.from_numpy((1.0 / wshots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    adjoint.misfit_and_gradient(wm, wgeo, torch.zeros((40, len(wshots[0].receivers)), device="cuda"))
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
     base = torch.cuda.memory_allocated()
