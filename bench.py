@@ -502,32 +502,44 @@ def run_b300(args, dist, rank, local, world):
     if rank == 0 and not args.skip_unfused:
         unfused = measure_unfused(shot, model, stream)
 
-    # ---- end to end: velocity up from pinned host memory, traces back, every step
+    # ---- end to end: velocity up from pinned host memory, traces back, every step.
+    # Two models on two streams take alternate shots, so one shot's upload and
+    # the previous shot's trace download run on the copy engines while the
+    # other model computes; every copy is inside the timed region.
     e2e = None
     if not args.skip_e2e:
         v_pinned = torch.from_numpy(shot.vel.ravel()).pin_memory()
-        tr_pinned = torch.empty((shot.nt, nrec), dtype=torch.float32).pin_memory()
+        tr_pinned = [torch.empty((shot.nt, nrec), dtype=torch.float32).pin_memory() for _ in range(2)]
         rec = shot.receivers
+        stream2 = torch.cuda.Stream()
+        models = [model, fd.Model.from_shot(shot, stream=stream2)]
 
-        def e2e_step():
-            fd.fd_set_velocity_ptr(model.handle, v_pinned.data_ptr())
-            model.set_source(shot.src, shot.wavelet)
-            model.set_receivers(rec)
-            model.run_shot(shot.nt)
-            fd.fd_gather_traces_ptr(model.handle, tr_pinned.data_ptr(), tr_pinned.numel())
+        def e2e_step(k):
+            m = models[k % 2]
+            fd.fd_set_velocity_ptr(m.handle, v_pinned.data_ptr())
+            m.set_source(shot.src, shot.wavelet)
+            m.set_receivers(rec)
+            m.run_shot(shot.nt)
+            fd.fd_gather_traces_async_ptr(m.handle, tr_pinned[k % 2].data_ptr(), tr_pinned[k % 2].numel())
 
-        e2e_step()
+        for k in range(2):
+            e2e_step(k)
+        for m in models:
+            fd.fd_synchronize(m.handle)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
+        for k in range(args.steps):
+            e2e_step(k)
+        for m in models:
+            fd.fd_synchronize(m.handle)
         el = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+        models[1].close()
         h2d = shot.vel.nbytes + shot.wavelet.nbytes + rec.nbytes
         d2h = shot.nt * nrec * 4
         e2e = {"value": world * args.steps * shot.nt * npts / el / 1e9, "unit": "Gupd/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "overlap": "two models on two streams alternate shots; uploads and downloads overlap compute"}
     model.close()
 
     cpu = None

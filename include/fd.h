@@ -146,6 +146,11 @@ fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev);
 /* Copy the recorded traces [rows][nrec] to host memory (cap = floats available;
  * FD_EINVAL if smaller than rows * nrec).  Synchronises the model's stream. */
 fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap);
+/* As fd_gather_traces, but only enqueues the copy on the model's stream and
+ * returns: host_out holds the traces once the stream has reached the copy
+ * (fd_synchronize, or an event).  With pinned host memory the copy overlaps
+ * kernels of other streams, e.g. the next shot of a second model. */
+fd_status fd_gather_traces_async(fd_model *m, float *host_out, size_t cap);
 
 /* Copy P (level n) and, if pold_host is not NULL, Pold (level n-1) to dense
  * host arrays of cap floats each.  Synchronises the model's stream. */

@@ -671,15 +671,25 @@ extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
     return fd_step(m, nt);
 }
 
-extern "C" fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap)
+extern "C" fd_status fd_gather_traces_async(fd_model *m, float *host_out, size_t cap)
 {
     NEED_MODEL(m);
     const size_t need = (size_t)m->trace_rows * m->nrec;
     if (need > 0 && (!host_out || cap < need))
         return fail(FD_EINVAL, "trace output needs %zu floats (got %zu)", need, cap);
+    if (m->pending_row >= 0)
+        if (fd_status st = flush_pending(m))
+            return st;
     if (need > 0 && m->traces)
         FD_CUDA(cudaMemcpyAsync(host_out, m->traces, need * sizeof(float), cudaMemcpyDeviceToHost, m->stream),
                 "trace download");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap)
+{
+    if (fd_status st = fd_gather_traces_async(m, host_out, cap))
+        return st;
     return fd_synchronize(m);
 }
 

@@ -41,7 +41,7 @@ EXPORTS = [
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
-    "fd_adjoint_segment",
+    "fd_adjoint_segment", "fd_gather_traces_async",
 ]
 
 
@@ -90,6 +90,7 @@ _SIGS = {
     "fd_step": (_i, [_vp, _i]),
     "fd_run_shot": (_i, [_vp, _i, _vp]),
     "fd_gather_traces": (_i, [_vp, _vp, _sz]),
+    "fd_gather_traces_async": (_i, [_vp, _vp, _sz]),
     "fd_get_wavefield": (_i, [_vp, _vp, _vp, _sz]),
     "fd_synchronize": (_i, [_vp]),
     "fd_get_step": (_i, [_vp, _ip]),
@@ -253,6 +254,11 @@ def fd_gather_traces(m: int, out: np.ndarray):
 def fd_gather_traces_ptr(m: int, host_ptr: int, cap: int):
     """fd_gather_traces into a raw host pointer (e.g. a pinned torch tensor)."""
     _check(_lib.fd_gather_traces(m, host_ptr, int(cap)), "fd_gather_traces")
+
+
+def fd_gather_traces_async_ptr(m: int, host_ptr: int, cap: int):
+    """Enqueue the trace download into a raw (pinned) host pointer; no synchronisation."""
+    _check(_lib.fd_gather_traces_async(m, host_ptr, int(cap)), "fd_gather_traces_async")
 
 
 def fd_get_wavefield(m: int, shape, with_old: bool = False):

@@ -252,3 +252,20 @@ def test_device_inputs_match_host_inputs(fdlib):
         fdlib.fd_synchronize(m.handle)
         np.testing.assert_array_equal(m.wavefield(), a[0])
     np.testing.assert_array_equal(traces.cpu().numpy(), a[2])
+
+
+def test_async_trace_gather(fdlib):
+    """fd_gather_traces_async enqueues the same copy as fd_gather_traces without
+    waiting; after fd_synchronize the pinned buffer holds the same traces."""
+    import torch
+    shot = wl.roofline_3d(shape=(33, 20, 40), nt=12, sponge_width=4)
+    with fdlib.Model.from_shot(shot) as m:
+        m.run_shot(shot.nt)
+        want = m.traces(shot.nt)
+        m.run_shot(shot.nt)
+        buf = torch.full((shot.nt, len(shot.receivers)), float("nan")).pin_memory()
+        fdlib.fd_gather_traces_async_ptr(m.handle, buf.data_ptr(), buf.numel())
+        fdlib.fd_synchronize(m.handle)
+        np.testing.assert_array_equal(buf.numpy(), want)
+        with pytest.raises(fdlib.FDError):
+            fdlib.fd_gather_traces_async_ptr(m.handle, buf.data_ptr(), buf.numel() - 1)
