@@ -10,7 +10,9 @@
 // velocity, and the receiver residuals enter as w g / (1 + a) at the receiver
 // points (fd_inject_receivers).  The gradient with respect to m is
 //   dJ/dm = -(1/m) sum_{n=0}^{nt-1} psi_{n+1} (L' P^n)
-// accumulated by fd_imaging (damping profiles held fixed).
+// (damping profiles held fixed), accumulated by fd_imaging from a stored P^n or
+// by fd_imaging_product from the L'P^n that fd_step_lp writes during the
+// segment recompute (fd_adjoint_segment issues a whole segment).
 
 #include <algorithm>
 
