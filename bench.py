@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
     ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
+    ap.add_argument("--batch-tile", type=int, default=-1,
+                    help="batched workload: tile variant (0: 64x16, 1: 64x32, 2: 128x16); -1 autotunes")
+    ap.add_argument("--group-mb", type=int, default=96, help="batched workload: group budget with --batch-tile")
     return ap.parse_args()
 
 
@@ -253,7 +256,7 @@ def run_reference(args, dist, rank, world):
 
 # ------------------------------------------------------------------------ batched 2D
 
-def measure_batched(nshots=64, nt=2000, repeats=1):
+def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
     """The batched 2D workload served two ways on this GPU: one shot at a time
     (fd_run_shot per shot, back to back) and all shots in one persistent batch
     (autotuned).  Returns a summary dict; results are compared bitwise."""
@@ -285,7 +288,11 @@ def measure_batched(nshots=64, nt=2000, repeats=1):
     ref = [m.traces(nt).copy() for m in models]
     ref_p = [m.wavefield() for m in models[:8]]
     batch = fd.Batch(models)
-    tuning = batch.autotune(trial_steps=20)
+    if tile >= 0:
+        batch.set_tuning(tile=tile, steps_per_launch=nt, ctas_per_sm=0, group_mb=group_mb)
+        tuning = batch.tuning()
+    else:
+        tuning = batch.autotune(trial_steps=20)
     launches0 = fd.fd_kernel_launch_count()
     t_batch = timed(lambda: batch.run_shots([nt] * nshots))
     batch_launches = (fd.fd_kernel_launch_count() - launches0) // (repeats + 1)
@@ -597,7 +604,8 @@ def run_batched_line(args, rank):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if rank != 0:
         return
-    r = measure_batched(args.shots, args.batch_nt, repeats=max(1, args.steps))
+    r = measure_batched(args.shots, args.batch_nt, repeats=max(1, args.steps), tile=args.batch_tile,
+                        group_mb=args.group_mb)
     line = {"metric": "shots/s (batched 2D)", "value": r["batched"]["shots_per_s"], "unit": "shots/s",
             "n_gpus": 1, "steps": max(1, args.steps), "warmup": 1, "ms_per_step": r["batched"]["s"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
