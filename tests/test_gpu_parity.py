@@ -269,3 +269,58 @@ def test_async_trace_gather(fdlib):
         np.testing.assert_array_equal(buf.numpy(), want)
         with pytest.raises(fdlib.FDError):
             fdlib.fd_gather_traces_async_ptr(m.handle, buf.data_ptr(), buf.numel() - 1)
+
+
+def _sample_points(shape, bz, rng, nrandom=200):
+    """Tile and chunk edges, faces, corners and random points of a grid."""
+    axes = []
+    for ax, n in enumerate(shape):
+        cand = {0, 1, 3, 4, 5, n // 2, n - 5, n - 4, n - 2, n - 1}
+        if ax == len(shape) - 1:
+            cand |= {31, 32, 33, 63, 64, 65}            # x tile edges (32 in 3D, 64 in 2D)
+        elif ax == 0 and len(shape) == 3:
+            cand |= {bz - 1, bz, bz + 1}                 # z chunk edge
+        else:
+            cand |= {15, 16, 17, 31, 32, 33}             # y / 2D z tile edges
+        axes.append(sorted(c for c in cand if 0 <= c < n))
+    grid = np.array(np.meshgrid(*axes, indexing="ij")).reshape(len(shape), -1).T
+    pick = grid[rng.choice(len(grid), size=min(len(grid), 400), replace=False)]
+    rnd = np.stack([rng.integers(0, n, nrandom) for n in shape], axis=1)
+    return np.concatenate([pick, rnd])
+
+
+@pytest.mark.parametrize("shape", [(520, 2050, 2046), (40000, 56000)])
+def test_parity_beyond_2pow31_points_sampled(fdlib, oracle, shape):
+    """Grids of more than 2^31 points, so every index path needs 64 bits: one step
+    from a random state, checked at sampled points (tile and chunk edges, faces,
+    corners, random points).  Each reference value is the oracle's step of the
+    point's radius-4 neighbourhood cut from the same inputs; no sponge, so the cut
+    sees the same coefficients, and where it meets a grid face the oracle's zero
+    halo is the grid's own."""
+    import torch
+    ndim = len(shape)
+    assert int(np.prod(shape)) > 2 ** 31
+    h = 10.0
+    dt = 0.4 * h / 2500.0
+    vel, P0, Pm1 = wl.device_random_fields(shape, seed=77)
+    out = torch.empty_like(P0)
+    with fdlib.Model(ndim, shape, h, dt, vel) as m:
+        fdlib.fd_set_wavefield_dev(m.handle, P0, Pm1, 0)
+        fdlib.fd_step(m.handle, 1)
+        fdlib.fd_get_wavefield_dev(m.handle, out)
+        torch.cuda.synchronize()
+    pts = _sample_points(shape, 512, np.random.default_rng(5))
+    idx = tuple(torch.from_numpy(pts[:, a]).cuda() for a in range(ndim))
+    got = out[idx].double().cpu().numpy()
+    ref = np.empty(len(pts))
+    for i, p in enumerate(pts):
+        lo = [max(0, c - 4) for c in p]
+        hi = [min(n, c + 5) for c, n in zip(p, shape)]
+        cut = tuple(slice(a, b) for a, b in zip(lo, hi))
+        Pn, _, _ = oracle.run(ndim, tuple(b - a for a, b in zip(lo, hi)), h, dt, vel[cut].cpu().numpy(),
+                              P=P0[cut].cpu().numpy(), Pold=Pm1[cut].cpu().numpy(), nsteps=1)
+        ref[i] = Pn[tuple(c - a for c, a in zip(p, lo))]
+    del vel, P0, Pm1, out
+    torch.cuda.empty_cache()
+    err = np.abs(got - ref) / np.max(np.abs(ref))
+    assert err.max() < 1e-5, (err.max(), pts[np.argmax(err)])

@@ -127,6 +127,18 @@ def random_state(shape, seed: int, scale: float = 1.0):
             rng.standard_normal(shape).astype(np.float32) * scale)
 
 
+def device_random_fields(shape, seed: int, vmin: float = 1500.0, vmax: float = 2500.0, device="cuda"):
+    """(vel, P, Pold) as FP32 torch tensors generated on the device from one seeded
+    generator: vel ~ U(vmin, vmax), P and Pold ~ N(0, 1).  For grids too large to
+    generate and upload from the host in a test (billions of points)."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    vel = torch.rand(shape, device=device, generator=g).mul_(vmax - vmin).add_(vmin)
+    P = torch.randn(shape, device=device, generator=g)
+    Pold = torch.randn(shape, device=device, generator=g)
+    return vel, P, Pold
+
+
 # ------------------------------------------------------------------------ workloads
 
 def parity_2d(nt: int = 500) -> Shot:
