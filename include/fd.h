@@ -148,8 +148,10 @@ fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev);
 fd_status fd_gather_traces(fd_model *m, float *host_out, size_t cap);
 /* As fd_gather_traces, but only enqueues the copy on the model's stream and
  * returns: host_out holds the traces once the stream has reached the copy
- * (fd_synchronize, or an event).  With pinned host memory the copy overlaps
- * kernels of other streams, e.g. the next shot of a second model. */
+ * (fd_synchronize, or an event), and must stay valid until then.  With pinned
+ * host memory the copy overlaps kernels of other streams, e.g. the next shot
+ * of a second model (with pageable memory CUDA may copy synchronously).
+ * FD_EINVAL if cap is smaller than rows * nrec. */
 fd_status fd_gather_traces_async(fd_model *m, float *host_out, size_t cap);
 
 /* Copy P (level n) and, if pold_host is not NULL, Pold (level n-1) to dense
@@ -200,10 +202,11 @@ fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_dev);
  * factor the imaging condition needs, produced while the forward segment is
  * recomputed, so the adjoint pass needs neither a copy of P^n nor a second
  * stencil. */
-fd_status fd_step_lp(fd_model *m, float *lp_dev);
+fd_status fd_step_lp(fd_model *m, float *lp_dev);   /* FD_EINVAL: NULL lp_dev (nx*ny*nz floats, the caller's) */
 /* grad_dev += P_adj * lp_dev pointwise over dense [nz][ny][nx] device arrays,
  * where P_adj is the current level of adj and lp_dev comes from fd_step_lp
- * (asynchronous on adj's stream). */
+ * (asynchronous on adj's stream; one FMA per point).  Both arrays belong to
+ * the caller.  FD_EINVAL for NULL arguments. */
 fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, float *grad_dev);
 /* One checkpoint segment [n0, n1) of the reverse-time adjoint, issued from the
  * host in one call (asynchronous; fwd and adj must share a stream and a grid).
