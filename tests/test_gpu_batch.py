@@ -145,3 +145,34 @@ def test_stalled_item_times_out_and_context_survives(fdlib):
     for m in models:
         m.close()
     assert_same(got, solo(fdlib, shots, [40, 40, 40]))
+
+
+def test_batched_workload_full_size_vs_oracle(fdlib, oracle):
+    """The 64-shot batched workload at its full grid sizes, every shot started from a
+    random state so that every tile is active, 10 steps in one batch; six shots (the
+    smallest, the largest and four seeded others) against the oracle, rel L2 <= 1e-4
+    for both levels and the traces."""
+    nt = 10
+    shots = [wl.batched_2d_shot(i, s, nt) for i, s in enumerate(wl.batched_2d_shapes(64))]
+    states = [wl.random_state(s.shape, seed=900 + i) for i, s in enumerate(shots)]
+    models = [fdlib.Model.from_shot(s) for s in shots]
+    try:
+        for m, (P0, Pm1) in zip(models, states):
+            fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
+            fdlib.fd_set_trace_buffer(m.handle, None, nt)
+        with fdlib.Batch(models) as b:
+            b.step(nt)
+        sizes = [s.npoints for s in shots]
+        pick = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+        pick |= set(np.random.default_rng(3).choice(64, 4, replace=False).tolist())
+        for i in sorted(pick):
+            s = shots[i]
+            (P, Pold), tr = models[i].wavefield(with_old=True), models[i].traces(nt)
+            rP, rPold, rtr = oracle.run(2, s.shape, s.h, s.dt, s.vel, sponge_width=s.sponge_width,
+                                        sponge_R=s.sponge_R, src=s.src, wavelet=s.wavelet, receivers=s.receivers,
+                                        P=states[i][0], Pold=states[i][1], nsteps=nt)
+            errs = (pl.rel_l2(P, rP), pl.rel_l2(Pold, rPold), pl.rel_l2(tr, rtr))
+            assert max(errs) <= 1e-4, (i, s.shape, errs)
+    finally:
+        for m in models:
+            m.close()
