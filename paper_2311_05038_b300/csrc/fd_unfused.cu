@@ -10,9 +10,11 @@
 // fd_time (the reading of the fused step), so both schedules compute the same
 // recurrence; only the summation order of the axes differs.
 //
-// Each derivative kernel: a thread owns 4 consecutive x points of one row and
-// forms, per axis, D2 = sum_k c_k ((P[+k] + P[-k]) - 2 P) with P = 0 outside
-// the grid, reading neighbours through L1/L2 with 16-byte loads.
+// Each derivative kernel forms, per axis, D2 = sum_k c_k ((P[+k] + P[-k]) - 2 P)
+// with P = 0 outside the grid, for 4 consecutive x points per thread with
+// 16-byte loads.  The x kernel reads its neighbours from the same row; the y
+// and z kernels march along their axis with the 9 values of the thread's
+// column in registers, so each value is loaded about once.
 
 #include <algorithm>
 
@@ -103,6 +105,58 @@ __global__ void __launch_bounds__(256) d2_kernel(const UnfusedParams p)
     } else {
         for (int e = 0; e < 4 && x + e < p.nx; ++e)
             dst[e] = r[e];
+    }
+}
+
+// D2 along y (AXIS 1) or z (AXIS 2) by marching: a block of 32 x 8 threads, each
+// thread 4 x points of one line along the axis (the lines of a block differ in
+// the other transverse coordinate; a 2D grid, ny = 1, spreads them along x
+// instead), kMarchLen points of the line per block with a 4-point halo at each
+// end.  Same arithmetic and order as d2_kernel.
+constexpr int kMarchLen = 64;
+
+template <int AXIS>
+__global__ void __launch_bounds__(256) d2_march_kernel(const UnfusedParams p)
+{
+    const int extent = AXIS == 1 ? p.ny : p.nz;
+    const int tdim = AXIS == 1 ? p.nz : p.ny;      // the other transverse coordinate
+    const bool flat = tdim == 1;
+    const int x = flat ? ((blockIdx.x * 8 + threadIdx.y) * 32 + threadIdx.x) * 4 : (blockIdx.x * 32 + threadIdx.x) * 4;
+    const int t = flat ? 0 : blockIdx.y * 8 + threadIdx.y;
+    if (x >= p.nx || t >= tdim)
+        return;
+    const int c0 = blockIdx.z * kMarchLen;
+    const int c1 = min(extent, c0 + kMarchLen);
+    const long long stride = AXIS == 1 ? (long long)p.px : (long long)p.ny * p.px;
+    const long long base = AXIS == 1 ? (long long)t * p.ny * p.px : (long long)t * p.px;
+    const float ck[4] = {p.c1, p.c2, p.c3, p.c4};
+    float4 q[9];   // q[i] = P at coordinate c - 4 + i of this column
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = c0 - 4 + i;
+        q[i] = c >= 0 && c < extent ? load4_or_zero(p.P, base + c * stride, x, p.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int c = c0; c < c1; ++c) {
+        q[8] = c + 4 < extent ? load4_or_zero(p.P, base + (c + 4) * stride, x, p.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float r[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int k = 1; k <= 4; ++k) {
+                const float d = fmaf(-2.f, comp(q[4], e), comp(q[4 + k], e) + comp(q[4 - k], e));
+                r[e] = k == 1 ? ck[0] * d : fmaf(ck[k - 1], d, r[e]);
+            }
+        }
+        float *dst = p.out + base + c * stride + x;
+        if (x + 3 < p.nx) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(r[0], r[1], r[2], r[3]);
+        } else {
+            for (int e = 0; e < 4 && x + e < p.nx; ++e)
+                dst[e] = r[e];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            q[i] = q[i + 1];
     }
 }
 
@@ -211,13 +265,20 @@ extern "C" fd_status fd_routine(fd_model *m, int routine)
         d2_kernel<0><<<blocks, 256, 0, m->stream>>>(p);
         break;
     case FD_ROUTINE_PYY:
-        p.out = m->deriv[1];
-        d2_kernel<1><<<blocks, 256, 0, m->stream>>>(p);
+    case FD_ROUTINE_PZZ: {
+        const bool y = routine == FD_ROUTINE_PYY;
+        p.out = m->deriv[y ? 1 : 2];
+        const int qx = (m->nx + 3) / 4;
+        const int extent = y ? m->ny : m->nz, tdim = y ? m->nz : m->ny;
+        const dim3 block(32, 8);
+        const dim3 grid(tdim == 1 ? (qx + 255) / 256 : (qx + 31) / 32, tdim == 1 ? 1 : (tdim + 7) / 8,
+                        (extent + kMarchLen - 1) / kMarchLen);
+        if (y)
+            d2_march_kernel<1><<<grid, block, 0, m->stream>>>(p);
+        else
+            d2_march_kernel<2><<<grid, block, 0, m->stream>>>(p);
         break;
-    case FD_ROUTINE_PZZ:
-        p.out = m->deriv[2];
-        d2_kernel<2><<<blocks, 256, 0, m->stream>>>(p);
-        break;
+    }
     case FD_ROUTINE_TIME:
         p.out = m->buf[m->cur ^ 1];
         p.d0 = m->deriv[0];

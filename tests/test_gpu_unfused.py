@@ -20,8 +20,9 @@ def run(fd, shot, nt, unfused):
         return m.wavefield(with_old=True), m.traces(nt)
 
 
-@pytest.mark.parametrize("shot", [wl.parity_2d(nt=300), wl.roofline_3d(shape=(40, 36, 70), nt=200, sponge_width=8)],
-                         ids=["2d", "3d"])
+@pytest.mark.parametrize("shot", [wl.parity_2d(nt=300), wl.roofline_3d(shape=(40, 36, 70), nt=200, sponge_width=8),
+                                  wl.roofline_3d(shape=(150, 70, 45), nt=40, sponge_width=6)],
+                         ids=["2d", "3d", "3d-long-axes"])
 def test_unfused_matches_oracle_and_fused(fdlib, oracle, shot):
     (P, Pold), tr = run(fdlib, shot, shot.nt, unfused=True)
     Pr, Poldr, trr = oracle.run(shot.ndim, shot.shape, shot.h, shot.dt, shot.vel, sponge_width=shot.sponge_width,
