@@ -149,7 +149,7 @@ def parity_2d(nt: int = 500) -> Shot:
     rec = np.array([(ix, 0, 64) for ix in range(0, 256, 4)], dtype=np.int32)
     return Shot(ndim=2, shape=(n, n), h=h, dt=dt, nt=nt, vel=vel, src=(128, 0, 128),
                 wavelet=ricker(nt, dt, f), receivers=rec, sponge_width=0,
-                name="2d-256x256-const2000-r4-500steps")
+                name=f"2d-256x256-const2000-r4-{nt}steps")
 
 
 def roofline_3d(n: int = 512, nt: int = 1000, sponge_width: int = 20, seed: int = 1,
