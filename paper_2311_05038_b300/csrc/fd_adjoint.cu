@@ -19,6 +19,7 @@
 #include "fd.h"
 #include "fd_internal.h"
 #include "fd_model.h"
+#include "fd_trace.h"
 
 namespace fdk {
 
@@ -209,6 +210,7 @@ extern "C" fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, floa
 extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, int n1, float *lp_buf,
                                         const float *g_dev, float *grad_dev)
 {
+    NvtxRange nvtx_range("fd_adjoint_segment");
     if (!fwd || !adj || !lp_buf || !grad_dev || (adj->nrec > 0 && !g_dev))
         return fail(FD_EINVAL, "fd_adjoint_segment: NULL argument");
     if (n0 < 0 || n1 <= n0)

@@ -26,6 +26,7 @@
 #include "fd.h"
 #include "fd_internal.h"
 #include "fd_model.h"
+#include "fd_trace.h"
 
 using namespace fdk;
 
@@ -234,6 +235,7 @@ static fd_status upload_damping(fd_model *m)
 // on failure.
 static fd_status load_velocity(fd_model *m, const float *v, cudaMemcpyKind kind)
 {
+    NvtxRange nvtx_range("load_velocity");
     if (!v)
         return fail(FD_EINVAL, "NULL velocity");
     if (!m->stage)
@@ -643,6 +645,7 @@ static fd_status step_n(fd_model *m, int nsteps, float *lp)
 
 extern "C" fd_status fd_step(fd_model *m, int nsteps)
 {
+    NvtxRange nvtx_range("fd_step");
     NEED_MODEL(m);
     if (nsteps < 0)
         return fail(FD_EINVAL, "nsteps must be >= 0");
@@ -651,6 +654,7 @@ extern "C" fd_status fd_step(fd_model *m, int nsteps)
 
 extern "C" fd_status fd_step_lp(fd_model *m, float *lp_dev)
 {
+    NvtxRange nvtx_range("fd_step_lp");
     NEED_MODEL(m);
     if (!lp_dev)
         return fail(FD_EINVAL, "fd_step_lp: NULL output");
@@ -659,6 +663,7 @@ extern "C" fd_status fd_step_lp(fd_model *m, float *lp_dev)
 
 extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
 {
+    NvtxRange nvtx_range("fd_run_shot");
     NEED_MODEL(m);
     if (nt < 0)
         return fail(FD_EINVAL, "nt must be >= 0");
@@ -673,6 +678,7 @@ extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
 
 extern "C" fd_status fd_gather_traces_async(fd_model *m, float *host_out, size_t cap)
 {
+    NvtxRange nvtx_range("fd_gather_traces");
     NEED_MODEL(m);
     const size_t need = (size_t)m->trace_rows * m->nrec;
     if (need > 0 && (!host_out || cap < need))

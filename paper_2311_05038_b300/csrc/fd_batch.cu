@@ -31,6 +31,7 @@
 #include "fd.h"
 #include "fd_internal.h"
 #include "fd_model.h"
+#include "fd_trace.h"
 #include "ptx.cuh"
 #include "stencil.cuh"
 
@@ -645,6 +646,7 @@ static fd_status capture_graph(fd_batch *b, const BatchParams &p)
 
 extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each)
 {
+    NvtxRange nvtx_range("fd_batch_step");
     if (!b)
         return fail(FD_EINVAL, "NULL batch");
     FD_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
@@ -746,6 +748,7 @@ std::string batch_signature(const fd_batch *b)
 
 extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best)
 {
+    NvtxRange nvtx_range("fd_batch_autotune");
     if (!b || trial_steps < 1)
         return fail(FD_EINVAL, "fd_batch_autotune: bad arguments");
     const std::string sig = batch_signature(b) + "/" + std::to_string(trial_steps);

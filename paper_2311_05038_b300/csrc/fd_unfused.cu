@@ -21,6 +21,7 @@
 #include "fd.h"
 #include "fd_internal.h"
 #include "fd_model.h"
+#include "fd_trace.h"
 
 namespace fdk {
 
@@ -321,6 +322,7 @@ extern "C" fd_status fd_routine(fd_model *m, int routine)
 
 extern "C" fd_status fd_step_unfused(fd_model *m, int nsteps)
 {
+    NvtxRange nvtx_range("fd_step_unfused");
     if (!m)
         return fail(FD_EINVAL, "NULL model");
     if (nsteps < 0)
