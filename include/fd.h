@@ -319,6 +319,14 @@ fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best)
  * Errors as fd_batch_step (FD_EINVAL, FD_EBUDGET, FD_ECUDA, FD_ETIMEOUT). */
 fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels, int nsteps);
 
+/* Test hook: fill the row padding of the model's device fields -- columns nx
+ * .. px-1 of every row of P, Pold, w and any unfused derivative field, where
+ * px is nx rounded up to 32 -- with NaN (asynchronous).  No kernel reads or
+ * writes those columns, so results stay finite and unchanged; tests use this
+ * in place of a memory checker.  fd_reset clears the padding again.  A no-op
+ * when nx is a multiple of 32. */
+fd_status fd_debug_poison_padding(fd_model *m);
+
 /* Number of CUDA kernel launches this library has issued since load. */
 uint64_t fd_kernel_launch_count(void);
 

@@ -676,6 +676,20 @@ extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
     return fd_step(m, nt);
 }
 
+extern "C" fd_status fd_debug_poison_padding(fd_model *m)
+{
+    NEED_MODEL(m);
+    if (m->px == m->nx)
+        return FD_OK;
+    const size_t pitch = (size_t)m->px * sizeof(float);
+    const size_t width = (size_t)(m->px - m->nx) * sizeof(float);
+    float *fields[6] = {m->buf[0], m->buf[1], m->w, m->deriv[0], m->deriv[1], m->deriv[2]};
+    for (float *f : fields)
+        if (f)   // all-ones bytes are a NaN in FP32
+            FD_CUDA(cudaMemset2DAsync(f + m->nx, pitch, 0xFF, width, m->rows, m->stream), "padding poison");
+    return FD_OK;
+}
+
 extern "C" fd_status fd_gather_traces_async(fd_model *m, float *host_out, size_t cap)
 {
     NvtxRange nvtx_range("fd_gather_traces");

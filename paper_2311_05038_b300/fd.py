@@ -41,7 +41,7 @@ EXPORTS = [
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
-    "fd_adjoint_segment", "fd_gather_traces_async",
+    "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding",
 ]
 
 
@@ -91,6 +91,7 @@ _SIGS = {
     "fd_run_shot": (_i, [_vp, _i, _vp]),
     "fd_gather_traces": (_i, [_vp, _vp, _sz]),
     "fd_gather_traces_async": (_i, [_vp, _vp, _sz]),
+    "fd_debug_poison_padding": (_i, [_vp]),
     "fd_get_wavefield": (_i, [_vp, _vp, _vp, _sz]),
     "fd_synchronize": (_i, [_vp]),
     "fd_get_step": (_i, [_vp, _ip]),
@@ -268,6 +269,11 @@ def fd_get_wavefield(m: int, shape, with_old: bool = False):
     _check(_lib.fd_get_wavefield(m, p.ctypes.data, None if po is None else po.ctypes.data, n),
            "fd_get_wavefield")
     return (p, po) if with_old else p
+
+
+def fd_debug_poison_padding(m: int):
+    """Test hook: NaN into the row padding (columns nx .. px-1) of the device fields."""
+    _check(_lib.fd_debug_poison_padding(m), "fd_debug_poison_padding")
 
 
 def fd_synchronize(m: int):

@@ -324,3 +324,43 @@ def test_parity_beyond_2pow31_points_sampled(fdlib, oracle, shape):
     torch.cuda.empty_cache()
     err = np.abs(got - ref) / np.max(np.abs(ref))
     assert err.max() < 1e-5, (err.max(), pts[np.argmax(err)])
+
+
+@pytest.mark.parametrize("shape", [(45, 38, 70), (53, 77)])
+@pytest.mark.parametrize("path", ["fused", "unfused", "lp"])
+def test_padding_canaries_never_reach_a_result(fdlib, oracle, shape, path):
+    """NaN in every row's padding (columns nx .. px-1 of P, Pold, w and the unfused
+    derivative fields) must never reach a result: every step path reads and writes
+    only the nx valid columns.  Checked against the oracle from a random state."""
+    import torch
+    ndim = len(shape)
+    nt = 12
+    rng = np.random.default_rng(8)
+    vel = rng.uniform(1500, 2500, shape).astype(np.float32)
+    dt = 0.4 * 10.0 / 2500.0
+    src = (shape[-1] // 3, shape[1] // 2 if ndim == 3 else 0, shape[0] // 2)
+    rec = np.array([(x, src[1], 5) for x in range(0, shape[-1], 5)], np.int32)
+    shot = wl.Shot(ndim, shape, 10.0, dt, nt, vel, src, wl.ricker(nt, dt, 30.0), rec, sponge_width=5)
+    P0, Pm1 = wl.random_state(shape, seed=81)
+    lp = torch.zeros(shape, device="cuda")
+    with fdlib.Model.from_shot(shot) as m:
+        fdlib.fd_set_trace_buffer(m.handle, None, nt)
+        fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
+        if path == "unfused":
+            fdlib.fd_routine(m.handle, fdlib.FD_ROUTINE_PXX)     # allocate the derivative fields
+        fdlib.fd_debug_poison_padding(m.handle)
+        if path == "fused":
+            fdlib.fd_step(m.handle, nt)
+        elif path == "unfused":
+            fdlib.fd_step_unfused(m.handle, nt)
+        else:
+            fdlib.fd_step_lp(m.handle, lp)
+            fdlib.fd_step(m.handle, nt - 1)
+        (P, Pold), tr = m.wavefield(with_old=True), m.traces(nt)
+    assert np.isfinite(P).all() and np.isfinite(Pold).all() and np.isfinite(tr).all()
+    rP, rPold, rtr = oracle.run(ndim, shape, 10.0, dt, vel, sponge_width=5, src=src, wavelet=shot.wavelet,
+                                receivers=rec, P=P0, Pold=Pm1, nsteps=nt)
+    assert max(pl.rel_l2(P, rP), pl.rel_l2(Pold, rPold), pl.rel_l2(tr, rtr)) <= 1e-4
+    if path == "lp":
+        got = lp.cpu().numpy()
+        assert np.isfinite(got).all() and pl.rel_l2(got, oracle.stencil_sum(P0)) <= 1e-6
