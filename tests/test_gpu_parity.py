@@ -326,8 +326,8 @@ def test_parity_beyond_2pow31_points_sampled(fdlib, oracle, shape):
     assert err.max() < 1e-5, (err.max(), pts[np.argmax(err)])
 
 
-@pytest.mark.parametrize("shape", [(45, 38, 70), (53, 77)])
-@pytest.mark.parametrize("path", ["fused", "unfused", "lp"])
+@pytest.mark.parametrize("shape,path", [(s, p) for s in [(45, 38, 70), (53, 77)]
+                                        for p in ("fused", "unfused", "lp", "batch") if len(s) == 2 or p != "batch"])
 def test_padding_canaries_never_reach_a_result(fdlib, oracle, shape, path):
     """NaN in every row's padding (columns nx .. px-1 of P, Pold, w and the unfused
     derivative fields) must never reach a result: every step path reads and writes
@@ -353,6 +353,9 @@ def test_padding_canaries_never_reach_a_result(fdlib, oracle, shape, path):
             fdlib.fd_step(m.handle, nt)
         elif path == "unfused":
             fdlib.fd_step_unfused(m.handle, nt)
+        elif path == "batch":
+            with fdlib.Batch([m]) as b:
+                b.step(nt)
         else:
             fdlib.fd_step_lp(m.handle, lp)
             fdlib.fd_step(m.handle, nt - 1)
