@@ -208,14 +208,24 @@ fd_status fd_step_lp(fd_model *m, float *lp_dev);   /* FD_EINVAL: NULL lp_dev (n
  * (asynchronous on adj's stream; one FMA per point).  Both arrays belong to
  * the caller.  FD_EINVAL for NULL arguments. */
 fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, float *grad_dev);
+/* One time step, as fd_step(m, 1), that also adds Pn * lp_dev to grad_dev
+ * pointwise (dense [nz][ny][nx] device arrays of the caller), Pn being the level
+ * the step produces: the imaging condition fused into the adjoint step, one pass
+ * over the grid instead of a step plus fd_imaging_product.  FD_EINVAL for NULL
+ * arrays. */
+fd_status fd_step_image(fd_model *m, const float *lp_dev, float *grad_dev);
+/* As fd_inject_receivers, and adds each injected value times lp_dev at its
+ * receiver point to grad_dev (dense arrays); after fd_step_image this makes the
+ * gradient update (level + injection) * lp_dev.  FD_EINVAL for NULL arrays. */
+fd_status fd_inject_receivers_image(fd_model *m, const float *values_dev, const float *lp_dev, float *grad_dev);
 /* One checkpoint segment [n0, n1) of the reverse-time adjoint, issued from the
  * host in one call (asynchronous; fwd and adj must share a stream and a grid).
  * The forward model fwd must be at step n0 (its levels n0 and n0-1 restored,
  * e.g. by fd_set_wavefield_dev); it advances n1 - n0 steps with fd_step_lp,
  * storing L'P^{n0+j} in lp_buf + j * nx*ny*nz (n1 - n0 dense fields, owned by
  * the caller).  Then for k = n1 down to n0 + 1 the adjoint model adj takes one
- * step, receives g_dev + (k-1) * nrec at its receivers (fd_inject_receivers)
- * and adds psi_k * L'P^{k-1} to grad_dev (fd_imaging_product).  Returns
+ * step, receives g_dev + (k-1) * nrec at its receivers, and psi_k * L'P^{k-1} is
+ * added to grad_dev (fd_step_image, fd_inject_receivers_image).  Returns
  * FD_EINVAL for bad arguments, FD_ESTATE if fwd is not at step n0. */
 fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, int n1, float *lp_buf, const float *g_dev,
                              float *grad_dev);

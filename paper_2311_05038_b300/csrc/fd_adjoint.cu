@@ -23,10 +23,13 @@
 
 namespace fdk {
 
-// values[r] * w / (1 + a) added to P at receiver r (pitched indices).
+// values[r] * w / (1 + a) added to P at receiver r (pitched indices); atomically,
+// since two receivers may share a point.  With grad set, the injected value times
+// lp is added to grad as well (dense indices), completing grad += P * lp for the
+// level P had before the injection.
 __global__ void inject_kernel(float *P, const float *w, const float *ax, const float *ay, const float *az,
                               const int64_t *idx, int nrec, const float *values, int nx, int ny, int px,
-                              int has_sponge, int ndim)
+                              int has_sponge, int ndim, const float *lp, float *grad)
 {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
         const int64_t i = idx[r];
@@ -39,7 +42,13 @@ __global__ void inject_kernel(float *P, const float *w, const float *ax, const f
             a = ax[x] + (ndim == 3 ? ay[y] : 0.f) + az[z];
         }
         const float v = values[r] * w[i];
-        P[i] += a != 0.f ? __fdividef(v, 1.0f + a) : v;
+        const float add = a != 0.f ? __fdividef(v, 1.0f + a) : v;
+        atomicAdd(&P[i], add);
+        if (grad) {
+            const int64_t row = i / px;
+            const int64_t d = row * nx + (i - row * px);
+            atomicAdd(&grad[d], add * lp[d]);
+        }
     }
 }
 
@@ -150,7 +159,7 @@ extern "C" fd_status fd_set_wavefield_dev(fd_model *m, const float *p_dev, const
     return FD_OK;
 }
 
-extern "C" fd_status fd_inject_receivers(fd_model *m, const float *values_dev)
+static fd_status inject(fd_model *m, const float *values_dev, const float *lp_dev, float *grad_dev)
 {
     if (!m || (m->nrec > 0 && !values_dev))
         return fail(FD_EINVAL, "fd_inject_receivers: bad arguments");
@@ -164,10 +173,24 @@ extern "C" fd_status fd_inject_receivers(fd_model *m, const float *values_dev)
     }
     const int blocks = std::min((m->nrec + 255) / 256, 1184);
     inject_kernel<<<blocks, 256, 0, m->stream>>>(m->buf[m->cur], m->w, m->ax, m->ay, m->az, m->d_rec, m->nrec,
-                                                 values_dev, m->nx, m->ny, m->px, m->has_sponge, m->d.ndim);
+                                                 values_dev, m->nx, m->ny, m->px, m->has_sponge, m->d.ndim, lp_dev,
+                                                 grad_dev);
     ++g_launches;
     FD_CUDA(cudaGetLastError(), "inject launch");
     return FD_OK;
+}
+
+extern "C" fd_status fd_inject_receivers(fd_model *m, const float *values_dev)
+{
+    return inject(m, values_dev, nullptr, nullptr);
+}
+
+extern "C" fd_status fd_inject_receivers_image(fd_model *m, const float *values_dev, const float *lp_dev,
+                                               float *grad_dev)
+{
+    if (!lp_dev || !grad_dev)
+        return fail(FD_EINVAL, "fd_inject_receivers_image: NULL argument");
+    return inject(m, values_dev, lp_dev, grad_dev);
 }
 
 extern "C" fd_status fd_imaging(fd_model *adj, const float *p_dev, float *grad_dev)
@@ -225,12 +248,14 @@ extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, in
     for (int j = 0; j < n1 - n0; ++j)
         if (fd_status st = fd_step_lp(fwd, lp_buf + (size_t)j * npts))
             return st;
+    // grad += psi_k * L'P^{k-1}: the step adds its new level times L'P, the
+    // injection adds its share, so the sum is (psi_k before + injected) * L'P
     for (int k = n1; k > n0; --k) {
-        if (fd_status st = fd_step(adj, 1))
+        const float *lp = lp_buf + (size_t)(k - 1 - n0) * npts;
+        if (fd_status st = fd_step_image(adj, lp, grad_dev))
             return st;
-        if (fd_status st = fd_inject_receivers(adj, adj->nrec > 0 ? g_dev + (size_t)(k - 1) * adj->nrec : nullptr))
-            return st;
-        if (fd_status st = fd_imaging_product(adj, lp_buf + (size_t)(k - 1 - n0) * npts, grad_dev))
+        if (fd_status st = fd_inject_receivers_image(
+                adj, adj->nrec > 0 ? g_dev + (size_t)(k - 1) * adj->nrec : nullptr, lp, grad_dev))
             return st;
     }
     return FD_OK;

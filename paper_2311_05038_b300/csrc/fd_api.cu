@@ -597,11 +597,15 @@ static fd_status flush_pending(fd_model *m)
 }
 
 // nsteps time steps; if lp is set (nsteps == 1), the step also writes L'P of the
-// level it consumes to lp (dense [nz][ny][nx]).
-static fd_status step_n(fd_model *m, int nsteps, float *lp)
+// level it consumes to lp; if img_grad is set (nsteps == 1), it adds Pn * img_lp
+// to img_grad (all dense [nz][ny][nx]).
+static fd_status step_n(fd_model *m, int nsteps, float *lp, const float *img_lp = nullptr,
+                        float *img_grad = nullptr)
 {
     StepParams p{};
     p.lp_out = lp;
+    p.img_lp = img_lp;
+    p.img_grad = img_grad;
     float w4[4];
     fd_stencil_weights(w4);
     p.c1 = w4[0];
@@ -659,6 +663,15 @@ extern "C" fd_status fd_step_lp(fd_model *m, float *lp_dev)
     if (!lp_dev)
         return fail(FD_EINVAL, "fd_step_lp: NULL output");
     return step_n(m, 1, lp_dev);
+}
+
+extern "C" fd_status fd_step_image(fd_model *m, const float *lp_dev, float *grad_dev)
+{
+    NvtxRange nvtx_range("fd_step_image");
+    NEED_MODEL(m);
+    if (!lp_dev || !grad_dev)
+        return fail(FD_EINVAL, "fd_step_image: NULL argument");
+    return step_n(m, 1, nullptr, lp_dev, grad_dev);
 }
 
 extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)

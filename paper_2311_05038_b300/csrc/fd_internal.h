@@ -69,13 +69,16 @@ struct StepParams {
     int nrec;
     float *trace_prev;        // if set: trace_prev[r] = P[rec_idx[r]] (previous step's row)
     float *lp_out;            // if set (the *_lp launches): L'P of level n, dense [nz][ny][nx]
+    const float *img_lp;      // if set (adjoint imaging launches): img_grad += Pn * img_lp,
+    float *img_grad;          //   both dense [nz][ny][nx]
     int *err;                 // device error word
 };
 
 size_t step3d_smem_bytes();
 cudaError_t step3d_prepare();
 int step3d_blocks_per_sm();
-// With p.lp_out set, the launch also writes the stencil sum L'P of level n.
+// With p.lp_out set, the launch also writes the stencil sum L'P of level n; with
+// p.img_grad set, it also adds Pn * p.img_lp to p.img_grad (the imaging condition).
 cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
                           const StepParams &p, int nchunks, cudaStream_t s);
 cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,

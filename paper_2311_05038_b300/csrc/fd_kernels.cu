@@ -49,9 +49,10 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 // ahead of the slowest warp without anyone blocking.  The only waits are the
 // bounded waits on the full barriers.
 //
-// With LP set the kernel also writes L'P (the stencil sum of level n) to the
-// dense array prm.lp_out, for the adjoint's imaging condition.
-template <int TX, int TY, int SP, int ST, int G, bool LP>
+// MODE 1 also writes L'P (the stencil sum of level n) to the dense array
+// prm.lp_out; MODE 2 also adds Pn * prm.img_lp to prm.img_grad.  Both serve the
+// adjoint's imaging condition; MODE 0 is the plain step.
+template <int TX, int TY, int SP, int ST, int G, int MODE>
 __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -253,13 +254,19 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
                 r[h] = __ffma2_rn(half2of(wv, h), acc[h], t);
             }
         }
-        if constexpr (LP) {
+        if constexpr (MODE == 1) {
             if (store_any)
                 store4_dense(prm.lp_out + ((size_t)(z0 + j) * prm.ny + y) * prm.nx + x, acc, prm.nx - x,
                              (prm.nx & 3) == 0);
         }
         if (src_col && z0 + j == prm.sz)
             add_source4(r, prm.sx - x, prm.src_amp);
+        if constexpr (MODE == 2) {
+            if (store_any) {
+                const size_t d = ((size_t)(z0 + j) * prm.ny + y) * prm.nx + x;
+                image4_dense(prm.img_grad + d, prm.img_lp + d, r, prm.nx - x, (prm.nx & 3) == 0);
+            }
+        }
         float *dst = out_col + (size_t)j * plane_stride;
         if (store_vec) {
             *reinterpret_cast<float4 *>(dst) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
@@ -339,7 +346,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
 // A CTA owns one TX x TZ tile of the [nz][nx] grid.  One TMA transaction brings
 // the haloed P tile and the Pold and w tiles; each thread computes 4
 // consecutive x points of one row.
-template <int TX, int TZ, bool LP>
+template <int TX, int TZ, int MODE>
 __global__ void __launch_bounds__(TX / 4 * TZ)
     step2d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -397,8 +404,11 @@ __global__ void __launch_bounds__(TX / 4 * TZ)
         add_source4(r, prm.sx - x, prm.src_amp);
     if (z < prm.nz && x < prm.nx) {
         store4(prm.out + (size_t)z * prm.px + x, r, prm.nx - x);
-        if constexpr (LP)
+        if constexpr (MODE == 1)
             store4_dense(prm.lp_out + (size_t)z * prm.nx + x, lp, prm.nx - x, (prm.nx & 3) == 0);
+        if constexpr (MODE == 2)
+            image4_dense(prm.img_grad + (size_t)z * prm.nx + x, prm.img_lp + (size_t)z * prm.nx + x, r,
+                         prm.nx - x, (prm.nx & 3) == 0);
     }
 }
 
@@ -450,7 +460,7 @@ __global__ void compute_w_kernel(const float *v, float *w, int nx, size_t rows, 
 
 // ------------------------------------------------------------------------ launchers
 
-#define FD_STEP3D(LP) step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3, LP>
+#define FD_STEP3D(MODE) step3d_kernel<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3, MODE>
 
 size_t step3d_smem_bytes()
 {
@@ -462,18 +472,19 @@ size_t step3d_smem_bytes()
 
 cudaError_t step3d_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(FD_STEP3D(false), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)step3d_smem_bytes());
+    const int bytes = (int)step3d_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(FD_STEP3D(0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(FD_STEP3D(true), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)step3d_smem_bytes());
+        e = cudaFuncSetAttribute(FD_STEP3D(1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
 int step3d_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FD_STEP3D(false), kThreads3, step3d_smem_bytes()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FD_STEP3D(0), kThreads3, step3d_smem_bytes()) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -485,9 +496,11 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
     const int tiles = ((p.nx + kTX3 - 1) / kTX3) * ((p.ny + kTY3 - 1) / kTY3);
     dim3 grid(tiles, nchunks);
     if (p.lp_out)
-        FD_STEP3D(true)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+        FD_STEP3D(1)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else if (p.img_grad)
+        FD_STEP3D(2)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     else
-        FD_STEP3D(false)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+        FD_STEP3D(0)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
 }
 
@@ -496,9 +509,11 @@ cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
 {
     const int tiles = ((p.nx + kTX2 - 1) / kTX2) * ((p.nz + kTZ2 - 1) / kTZ2);
     if (p.lp_out)
-        step2d_kernel<kTX2, kTZ2, true><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+        step2d_kernel<kTX2, kTZ2, 1><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    else if (p.img_grad)
+        step2d_kernel<kTX2, kTZ2, 2><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
     else
-        step2d_kernel<kTX2, kTZ2, false><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+        step2d_kernel<kTX2, kTZ2, 0><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
 }
 

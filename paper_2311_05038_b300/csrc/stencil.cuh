@@ -144,6 +144,27 @@ __device__ __forceinline__ void store4_dense(float *dst, const float2 (&v)[2], i
     }
 }
 
+// grad[e] = fma(v[e], lp[e], grad[e]) for 4 consecutive points of a dense row at
+// grad / lp (any alignment), of which the first is inside the row and `valid` are.
+__device__ __forceinline__ void image4_dense(float *grad, const float *lp, const float2 (&v)[2], int valid,
+                                             bool aligned)
+{
+    if (aligned && valid >= 4) {
+        const float4 l = *reinterpret_cast<const float4 *>(lp);
+        float4 g = *reinterpret_cast<const float4 *>(grad);
+        g.x = fmaf(v[0].x, l.x, g.x);
+        g.y = fmaf(v[0].y, l.y, g.y);
+        g.z = fmaf(v[1].x, l.z, g.z);
+        g.w = fmaf(v[1].y, l.w, g.w);
+        *reinterpret_cast<float4 *>(grad) = g;
+    } else {
+        grad[0] = fmaf(v[0].x, lp[0], grad[0]);
+        if (valid > 1) grad[1] = fmaf(v[0].y, lp[1], grad[1]);
+        if (valid > 2) grad[2] = fmaf(v[1].x, lp[2], grad[2]);
+        if (valid > 3) grad[3] = fmaf(v[1].y, lp[3], grad[3]);
+    }
+}
+
 // Store 4 consecutive points, of which the first is known to be inside the row.
 __device__ __forceinline__ void store4(float *dst, const float2 (&r)[2], int valid)
 {

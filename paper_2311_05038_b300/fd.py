@@ -41,7 +41,8 @@ EXPORTS = [
     "fd_batch_autotune", "fd_batch_step_noalloc", "fd_routine", "fd_step_unfused",
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
-    "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding",
+    "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
+    "fd_inject_receivers_image",
 ]
 
 
@@ -92,6 +93,8 @@ _SIGS = {
     "fd_gather_traces": (_i, [_vp, _vp, _sz]),
     "fd_gather_traces_async": (_i, [_vp, _vp, _sz]),
     "fd_debug_poison_padding": (_i, [_vp]),
+    "fd_step_image": (_i, [_vp, _vp, _vp]),
+    "fd_inject_receivers_image": (_i, [_vp, _vp, _vp, _vp]),
     "fd_get_wavefield": (_i, [_vp, _vp, _vp, _sz]),
     "fd_synchronize": (_i, [_vp]),
     "fd_get_step": (_i, [_vp, _ip]),
@@ -394,6 +397,17 @@ def fd_step_lp(m: int, lp_dev):
 def fd_imaging_product(adj: int, lp_dev, grad_dev):
     """grad_dev += (adj's current level) * lp_dev, pointwise."""
     _check(_lib.fd_imaging_product(adj, _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_imaging_product")
+
+
+def fd_step_image(m: int, lp_dev, grad_dev):
+    """One step that also adds the new level times lp_dev to grad_dev (dense)."""
+    _check(_lib.fd_step_image(m, _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_step_image")
+
+
+def fd_inject_receivers_image(m: int, values_dev, lp_dev, grad_dev):
+    """fd_inject_receivers, also adding each injected value times lp_dev to grad_dev."""
+    _check(_lib.fd_inject_receivers_image(m, None if values_dev is None else _dev_ptr(values_dev),
+                                          _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_inject_receivers_image")
 
 
 def fd_adjoint_segment(fwd: int, adj: int, n0: int, n1: int, lp_buf, g_dev, grad_dev):

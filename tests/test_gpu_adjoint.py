@@ -173,8 +173,8 @@ def _segment_case(fdlib, shape, seed):
 
 @pytest.mark.parametrize("shape", [(21, 17, 29), (33, 45)])
 def test_adjoint_segment_equals_step_by_step_calls(fdlib, shape):
-    """fd_adjoint_segment issues exactly fd_step_lp x (n1-n0), then per k fd_step,
-    fd_inject_receivers and fd_imaging_product: results bitwise equal."""
+    """fd_adjoint_segment issues exactly fd_step_lp x (n1-n0), then per k
+    fd_step_image and fd_inject_receivers_image: results bitwise equal."""
     import torch
     shot = _segment_case(fdlib, shape, seed=5)
     n0, n1 = 3, 9
@@ -194,9 +194,8 @@ def test_adjoint_segment_equals_step_by_step_calls(fdlib, shape):
                 for j in range(n1 - n0):
                     fdlib.fd_step_lp(fwd.handle, lp[j])
                 for k in range(n1, n0, -1):
-                    fdlib.fd_step(adj.handle, 1)
-                    fdlib.fd_inject_receivers(adj.handle, g[k - 1])
-                    fdlib.fd_imaging_product(adj.handle, lp[k - 1 - n0], grad)
+                    fdlib.fd_step_image(adj.handle, lp[k - 1 - n0], grad)
+                    fdlib.fd_inject_receivers_image(adj.handle, g[k - 1], lp[k - 1 - n0], grad)
             torch.cuda.synchronize()
             out.append((lp.cpu().numpy(), grad.cpu().numpy(), adj.wavefield()))
     for a, b in zip(out[0], out[1]):
@@ -267,3 +266,44 @@ def test_gradient_full_size_finite_differences(fdlib):
         dobs = torch.from_numpy(mt.traces(s.nt)).cuda()
     blob = torch.from_numpy((v_true.astype(np.float64) / s.vel - 1.0).astype(np.float32)).cuda()
     check(dobs, -2.0 * blob * m, 0.05, 1e-2, "anomaly data, blob direction")
+
+
+@pytest.mark.parametrize("shape", [(21, 17, 29), (33, 45), (20, 16, 32)])
+def test_fused_imaging_equals_separate_calls(fdlib, shape):
+    """fd_step_image is fd_step followed by fd_imaging_product, bitwise (the same FMA
+    on the same level); fd_inject_receivers_image adds its share so that the whole
+    equals (level + injection) * lp up to one rounding at the receivers."""
+    import torch
+    shot = _segment_case(fdlib, shape, seed=9)
+    P, Po = wl.random_state(shape, seed=31)
+    lp = torch.from_numpy(wl.random_state(shape, seed=32)[0]).cuda()
+    vals = torch.from_numpy(np.random.default_rng(33).standard_normal(len(shot.receivers)).astype(np.float32)).cuda()
+    g0 = torch.from_numpy(wl.random_state(shape, seed=34)[0]).cuda()
+    out = {}
+    for how in ("fused", "separate"):
+        with fdlib.Model.from_shot(shot) as m:
+            fdlib.fd_set_wavefield(m.handle, P, Po, 0)
+            grad = g0.clone()
+            if how == "fused":
+                fdlib.fd_step_image(m.handle, lp, grad)
+                torch.cuda.synchronize()
+                out["after_step"] = grad.cpu().numpy()
+                fdlib.fd_inject_receivers_image(m.handle, vals, lp, grad)
+            else:
+                fdlib.fd_step(m.handle, 1)
+                fdlib.fd_imaging_product(m.handle, lp, grad)
+                torch.cuda.synchronize()
+                out["after_step_sep"] = grad.cpu().numpy()
+                grad = g0.clone()
+                fdlib.fd_step(m.handle, 0)
+                # separate path of the whole update: step, inject, then one product
+                fdlib.fd_set_wavefield(m.handle, P, Po, 0)
+                fdlib.fd_step(m.handle, 1)
+                fdlib.fd_inject_receivers(m.handle, vals)
+                fdlib.fd_imaging_product(m.handle, lp, grad)
+            torch.cuda.synchronize()
+            out[how] = (m.wavefield(), grad.cpu().numpy())
+    np.testing.assert_array_equal(out["after_step"], out["after_step_sep"])
+    np.testing.assert_array_equal(out["fused"][0], out["separate"][0])
+    assert pl.rel_l2(out["fused"][1], out["separate"][1]) <= 1e-6
+
