@@ -54,9 +54,9 @@ __device__ __forceinline__ float comp(const float4 &v, int e)
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
-// axis 0 = x, 1 = y, 2 = z
-template <int AXIS>
-__global__ void __launch_bounds__(256) d2_kernel(const UnfusedParams p)
+// D2 along x: a thread owns 4 consecutive x points of one row and reads its
+// neighbours from the same row.
+__global__ void __launch_bounds__(256) d2x_kernel(const UnfusedParams p)
 {
     const int qx = (p.nx + 3) / 4;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,40 +65,19 @@ __global__ void __launch_bounds__(256) d2_kernel(const UnfusedParams p)
         return;
     const int x = (int)(i % qx) * 4;
     const long long row = i / qx;
-    const int y = (int)(row % p.ny);
-    const int z = (int)(row / p.ny);
     const long long base = row * p.px;
     const float4 c = load4_or_zero(p.P, base, x, p.nx);
-    float r[4] = {0.f, 0.f, 0.f, 0.f};
-    if (AXIS == 0) {
-        const float4 m = load4_or_zero(p.P, base, x - 4, p.nx);
-        const float4 q = load4_or_zero(p.P, base, x + 4, p.nx);
-        const float a[12] = {m.x, m.y, m.z, m.w, c.x, c.y, c.z, c.w, q.x, q.y, q.z, q.w};
+    const float4 m = load4_or_zero(p.P, base, x - 4, p.nx);
+    const float4 q = load4_or_zero(p.P, base, x + 4, p.nx);
+    const float a[12] = {m.x, m.y, m.z, m.w, c.x, c.y, c.z, c.w, q.x, q.y, q.z, q.w};
+    float r[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float pc = a[4 + e];
-            r[e] = p.c1 * fmaf(-2.f, pc, a[5 + e] + a[3 + e]);
-            r[e] = fmaf(p.c2, fmaf(-2.f, pc, a[6 + e] + a[2 + e]), r[e]);
-            r[e] = fmaf(p.c3, fmaf(-2.f, pc, a[7 + e] + a[1 + e]), r[e]);
-            r[e] = fmaf(p.c4, fmaf(-2.f, pc, a[8 + e] + a[0 + e]), r[e]);
-        }
-    } else {
-        const int coord = AXIS == 1 ? y : z;
-        const int extent = AXIS == 1 ? p.ny : p.nz;
-        const long long stride = AXIS == 1 ? (long long)p.px : (long long)p.ny * p.px;
-        const float ck[4] = {p.c1, p.c2, p.c3, p.c4};
-#pragma unroll
-        for (int k = 1; k <= 4; ++k) {
-            const float4 up = coord + k < extent ? load4_or_zero(p.P, base + k * stride, x, p.nx)
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 dn = coord - k >= 0 ? load4_or_zero(p.P, base - k * stride, x, p.nx)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float d = fmaf(-2.f, comp(c, e), comp(up, e) + comp(dn, e));
-                r[e] = k == 1 ? ck[0] * d : fmaf(ck[k - 1], d, r[e]);
-            }
-        }
+    for (int e = 0; e < 4; ++e) {
+        const float pc = a[4 + e];
+        r[e] = p.c1 * fmaf(-2.f, pc, a[5 + e] + a[3 + e]);
+        r[e] = fmaf(p.c2, fmaf(-2.f, pc, a[6 + e] + a[2 + e]), r[e]);
+        r[e] = fmaf(p.c3, fmaf(-2.f, pc, a[7 + e] + a[1 + e]), r[e]);
+        r[e] = fmaf(p.c4, fmaf(-2.f, pc, a[8 + e] + a[0 + e]), r[e]);
     }
     float *dst = p.out + base + x;
     if (x + 3 < p.nx) {
@@ -113,7 +92,7 @@ __global__ void __launch_bounds__(256) d2_kernel(const UnfusedParams p)
 // thread 4 x points of one line along the axis (the lines of a block differ in
 // the other transverse coordinate; a 2D grid, ny = 1, spreads them along x
 // instead), kMarchLen points of the line per block with a 4-point halo at each
-// end.  Same arithmetic and order as d2_kernel.
+// end.  Same arithmetic and order as d2x_kernel, along the other axis.
 constexpr int kMarchLen = 64;
 
 template <int AXIS>
@@ -263,7 +242,7 @@ extern "C" fd_status fd_routine(fd_model *m, int routine)
     switch (routine) {
     case FD_ROUTINE_PXX:
         p.out = m->deriv[0];
-        d2_kernel<0><<<blocks, 256, 0, m->stream>>>(p);
+        d2x_kernel<<<blocks, 256, 0, m->stream>>>(p);
         break;
     case FD_ROUTINE_PYY:
     case FD_ROUTINE_PZZ: {
