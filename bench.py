@@ -415,10 +415,27 @@ def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
             adjoint.Propagate.apply(m0, geo)
     torch.cuda.synchronize()
     fwd = time.perf_counter() - t0
+    # the same gradient keeping every L'P^n instead of checkpoints (nt fields per shot)
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    t0 = time.perf_counter()
+    grad_s = torch.zeros_like(m0)
+    for s, dobs in zip(shots, observed):
+        geo = adjoint.Geometry.from_shot(s, sponge_vmax=vmax, store_all=True)
+        grad_s += adjoint.misfit_and_gradient(m0, geo, dobs)[1]
+    torch.cuda.synchronize()
+    el_s = time.perf_counter() - t0
+    peak_s = torch.cuda.max_memory_allocated() - base
+    same = bool(torch.equal(grad, grad_s))
+    del grad_s
+    torch.cuda.empty_cache()
     return {"workload": f"{nshots} shots, {n}^3, {nt} steps, checkpoints every {checkpoint_every}",
             "s_per_gradient": el, "forward_s": fwd, "gradient_over_forward": el / fwd, "misfit": J,
             "peak_torch_memory_gb": peak / 1e9, "gupd_forward_equivalent": nshots * nt * n ** 3 / el / 1e9,
-            "grad_norm": float(grad.norm())}
+            "grad_norm": float(grad.norm()),
+            "store_all": {"s_per_gradient": el_s, "gradient_over_forward": el_s / fwd,
+                          "peak_torch_memory_gb": peak_s / 1e9, "gradient_identical": same}}
 
 
 # ------------------------------------------------------------------------ unfused 3D

@@ -218,6 +218,19 @@ fd_status fd_step_image(fd_model *m, const float *lp_dev, float *grad_dev);
  * receiver point to grad_dev (dense arrays); after fd_step_image this makes the
  * gradient update (level + injection) * lp_dev.  FD_EINVAL for NULL arrays. */
 fd_status fd_inject_receivers_image(fd_model *m, const float *values_dev, const float *lp_dev, float *grad_dev);
+/* nsteps >= 0 calls of fd_step_lp, the j-th writing lp_buf + j * nx*ny*nz
+ * (nsteps dense fields, the caller's): the forward pass of an adjoint that keeps
+ * every L'P^n instead of checkpoints (HBM permitting).  FD_EINVAL for a NULL
+ * buffer with nsteps > 0. */
+fd_status fd_step_lp_n(fd_model *m, int nsteps, float *lp_buf);
+/* The backward half of fd_adjoint_segment: for k = n1 down to n0 + 1 the adjoint
+ * model adj takes one step (fd_step_image with lp_buf + (k-1-n0) * nx*ny*nz) and
+ * receives g_dev + (k-1) * nrec (fd_inject_receivers_image), adding
+ * psi_k * L'P^{k-1} to grad_dev.  With the L'P^n of a whole run stored by
+ * fd_step_lp_n, one call with n0 = 0, n1 = nt needs no recompute.  FD_EINVAL for
+ * bad arguments.  Asynchronous on adj's stream. */
+fd_status fd_adjoint_backward(fd_model *adj, int n0, int n1, const float *lp_buf, const float *g_dev,
+                              float *grad_dev);
 /* One checkpoint segment [n0, n1) of the reverse-time adjoint, issued from the
  * host in one call (asynchronous; fwd and adj must share a stream and a grid).
  * The forward model fwd must be at step n0 (its levels n0 and n0-1 restored,

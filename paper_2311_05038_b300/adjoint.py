@@ -18,9 +18,15 @@ Memory is bounded by checkpointing: the forward pass keeps (P, Pold) every
 and recomputes each segment from its checkpoint with ``fd_step_lp``, which
 stores the stencil sums L'P^n the imaging condition needs (one field per step
 of the segment) instead of the levels themselves.  The adjoint then runs through
-the segment, and ``fd_imaging_product`` adds psi_{n+1} L'P^n pointwise; one
+the segment, each adjoint step adding psi_{n+1} L'P^n to the gradient as it
+goes (``fd_step_image``, ``fd_inject_receivers_image``); one
 ``fd_adjoint_segment`` call issues a whole segment from native code.  The
 forward work is therefore done twice, and no stencil is evaluated a third time.
+
+With ``store_all`` the forward pass keeps every L'P^n instead (``fd_step_lp_n``;
+nt fields, 100 GB for 256^3 x 1500 steps, which the B300's HBM holds) and the
+backward pass runs the adjoint straight through them (``fd_adjoint_backward``)
+without recomputing: the same gradient, bitwise, in less time.
 """
 from __future__ import annotations
 
@@ -46,11 +52,12 @@ class Geometry:
     sponge_R: float = 1e-3
     sponge_vmax: float | None = None
     checkpoint_every: int = 50
+    store_all: bool = False     # keep every L'P^n (nt fields) instead of checkpoints
 
     @classmethod
-    def from_shot(cls, shot, checkpoint_every=50, sponge_vmax=None):
+    def from_shot(cls, shot, checkpoint_every=50, sponge_vmax=None, store_all=False):
         return cls(shot.ndim, tuple(shot.shape), shot.h, shot.dt, shot.nt, shot.src, shot.wavelet, shot.receivers,
-                   shot.sponge_width, shot.sponge_R, sponge_vmax, checkpoint_every)
+                   shot.sponge_width, shot.sponge_R, sponge_vmax, checkpoint_every, store_all)
 
 
 def _model(torch, geo: Geometry, v, with_source: bool):
@@ -90,19 +97,25 @@ def _make_function():
             traces = torch.zeros((geo.nt, nrec), device=m.device, dtype=torch.float32)
             fd.fd_reset(model.handle)
             fd.fd_set_trace_buffer(model.handle, traces, geo.nt)
-            K = max(1, int(geo.checkpoint_every))
             ckpts = []
-            for n0 in range(0, geo.nt, K):
-                P = torch.empty(geo.shape, device=m.device, dtype=torch.float32)
-                Po = torch.empty_like(P)
-                fd.fd_get_wavefield_dev(model.handle, P, Po)
-                ckpts.append((P, Po))
-                fd.fd_step(model.handle, min(K, geo.nt - n0))
+            lp_all = None
+            if geo.store_all:
+                lp_all = torch.empty((geo.nt,) + tuple(geo.shape), device=m.device, dtype=torch.float32)
+                fd.fd_step_lp_n(model.handle, geo.nt, lp_all)           # lp_all[n] = L'P^n
+            else:
+                K = max(1, int(geo.checkpoint_every))
+                for n0 in range(0, geo.nt, K):
+                    P = torch.empty(geo.shape, device=m.device, dtype=torch.float32)
+                    Po = torch.empty_like(P)
+                    fd.fd_get_wavefield_dev(model.handle, P, Po)
+                    ckpts.append((P, Po))
+                    fd.fd_step(model.handle, min(K, geo.nt - n0))
             fd.fd_synchronize(model.handle)
             ctx.geo = geo
             ctx.model = model
             ctx.v = v
             ctx.ckpts = ckpts
+            ctx.lp_all = lp_all
             ctx.save_for_backward(m)
             return traces
 
@@ -114,9 +127,13 @@ def _make_function():
             K = max(1, int(geo.checkpoint_every))
             adj = _model(torch, geo, v, with_source=False)
             fd.fd_reset(adj.handle)
-            fd.fd_set_trace_buffer(model.handle, None, 0)       # recompute without recording
-            seg = torch.empty((K,) + tuple(geo.shape), device=m.device, dtype=torch.float32)
             acc = torch.zeros(geo.shape, device=m.device, dtype=torch.float32)
+            if ctx.lp_all is not None:
+                # every L'P^n is stored: the adjoint runs back through them at once
+                fd.fd_adjoint_backward(adj.handle, 0, geo.nt, ctx.lp_all, g, acc)
+                ctx.lp_all = None
+            fd.fd_set_trace_buffer(model.handle, None, 0)       # recompute without recording
+            seg = torch.empty((K,) + tuple(geo.shape), device=m.device, dtype=torch.float32) if ctx.ckpts else None
             for s in range(len(ctx.ckpts) - 1, -1, -1):
                 n0 = s * K
                 n1 = min(n0 + K, geo.nt)

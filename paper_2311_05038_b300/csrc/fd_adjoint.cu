@@ -230,6 +230,28 @@ extern "C" fd_status fd_imaging_product(fd_model *adj, const float *lp_dev, floa
     return FD_OK;
 }
 
+extern "C" fd_status fd_adjoint_backward(fd_model *adj, int n0, int n1, const float *lp_buf, const float *g_dev,
+                                         float *grad_dev)
+{
+    NvtxRange nvtx_range("fd_adjoint_backward");
+    if (!adj || !lp_buf || !grad_dev || (adj->nrec > 0 && !g_dev))
+        return fail(FD_EINVAL, "fd_adjoint_backward: NULL argument");
+    if (n0 < 0 || n1 <= n0)
+        return fail(FD_EINVAL, "fd_adjoint_backward: need 0 <= n0 < n1 (got %d, %d)", n0, n1);
+    const size_t npts = (size_t)adj->nx * adj->ny * adj->nz;
+    // grad += psi_k * L'P^{k-1}: the step adds its new level times L'P, the
+    // injection adds its share, so the sum is (psi_k before + injected) * L'P
+    for (int k = n1; k > n0; --k) {
+        const float *lp = lp_buf + (size_t)(k - 1 - n0) * npts;
+        if (fd_status st = fd_step_image(adj, lp, grad_dev))
+            return st;
+        if (fd_status st = fd_inject_receivers_image(
+                adj, adj->nrec > 0 ? g_dev + (size_t)(k - 1) * adj->nrec : nullptr, lp, grad_dev))
+            return st;
+    }
+    return FD_OK;
+}
+
 extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, int n1, float *lp_buf,
                                         const float *g_dev, float *grad_dev)
 {
@@ -248,15 +270,5 @@ extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, in
     for (int j = 0; j < n1 - n0; ++j)
         if (fd_status st = fd_step_lp(fwd, lp_buf + (size_t)j * npts))
             return st;
-    // grad += psi_k * L'P^{k-1}: the step adds its new level times L'P, the
-    // injection adds its share, so the sum is (psi_k before + injected) * L'P
-    for (int k = n1; k > n0; --k) {
-        const float *lp = lp_buf + (size_t)(k - 1 - n0) * npts;
-        if (fd_status st = fd_step_image(adj, lp, grad_dev))
-            return st;
-        if (fd_status st = fd_inject_receivers_image(
-                adj, adj->nrec > 0 ? g_dev + (size_t)(k - 1) * adj->nrec : nullptr, lp, grad_dev))
-            return st;
-    }
-    return FD_OK;
+    return fd_adjoint_backward(adj, n0, n1, lp_buf, g_dev, grad_dev);
 }

@@ -665,6 +665,19 @@ extern "C" fd_status fd_step_lp(fd_model *m, float *lp_dev)
     return step_n(m, 1, lp_dev);
 }
 
+extern "C" fd_status fd_step_lp_n(fd_model *m, int nsteps, float *lp_buf)
+{
+    NvtxRange nvtx_range("fd_step_lp_n");
+    NEED_MODEL(m);
+    if (nsteps < 0 || (nsteps > 0 && !lp_buf))
+        return fail(FD_EINVAL, "fd_step_lp_n: bad arguments");
+    const size_t npts = (size_t)m->nx * m->ny * m->nz;
+    for (int j = 0; j < nsteps; ++j)
+        if (fd_status st = step_n(m, 1, lp_buf + (size_t)j * npts))
+            return st;
+    return FD_OK;
+}
+
 extern "C" fd_status fd_step_image(fd_model *m, const float *lp_dev, float *grad_dev)
 {
     NvtxRange nvtx_range("fd_step_image");

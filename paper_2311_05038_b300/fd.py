@@ -42,7 +42,7 @@ EXPORTS = [
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
     "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
-    "fd_inject_receivers_image",
+    "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward",
 ]
 
 
@@ -95,6 +95,8 @@ _SIGS = {
     "fd_debug_poison_padding": (_i, [_vp]),
     "fd_step_image": (_i, [_vp, _vp, _vp]),
     "fd_inject_receivers_image": (_i, [_vp, _vp, _vp, _vp]),
+    "fd_step_lp_n": (_i, [_vp, _i, _vp]),
+    "fd_adjoint_backward": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "fd_get_wavefield": (_i, [_vp, _vp, _vp, _sz]),
     "fd_synchronize": (_i, [_vp]),
     "fd_get_step": (_i, [_vp, _ip]),
@@ -408,6 +410,18 @@ def fd_inject_receivers_image(m: int, values_dev, lp_dev, grad_dev):
     """fd_inject_receivers, also adding each injected value times lp_dev to grad_dev."""
     _check(_lib.fd_inject_receivers_image(m, None if values_dev is None else _dev_ptr(values_dev),
                                           _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_inject_receivers_image")
+
+
+def fd_step_lp_n(m: int, nsteps: int, lp_buf):
+    """nsteps steps, the j-th writing L'P of its consumed level to lp_buf[j]."""
+    _check(_lib.fd_step_lp_n(m, int(nsteps), _dev_ptr(lp_buf)), "fd_step_lp_n")
+
+
+def fd_adjoint_backward(adj: int, n0: int, n1: int, lp_buf, g_dev, grad_dev):
+    """The adjoint back from n1 to n0 through stored L'P fields lp_buf[0 .. n1-n0-1]."""
+    _check(_lib.fd_adjoint_backward(adj, int(n0), int(n1), _dev_ptr(lp_buf),
+                                    None if g_dev is None else _dev_ptr(g_dev), _dev_ptr(grad_dev)),
+           "fd_adjoint_backward")
 
 
 def fd_adjoint_segment(fwd: int, adj: int, n0: int, n1: int, lp_buf, g_dev, grad_dev):

@@ -307,3 +307,21 @@ def test_fused_imaging_equals_separate_calls(fdlib, shape):
     np.testing.assert_array_equal(out["fused"][0], out["separate"][0])
     assert pl.rel_l2(out["fused"][1], out["separate"][1]) <= 1e-6
 
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_store_all_gradient_equals_checkpointed(fdlib, ndim):
+    """Keeping every L'P^n (no recompute) gives the checkpointed gradient bitwise:
+    the recompute reproduces the forward levels exactly."""
+    import torch
+    from paper_2311_05038_b300 import adjoint
+    shot, vt = case(ndim, nt=90, seed=6)
+    dobs = observed(fdlib, shot, vt, 3200.0)
+    m = torch.from_numpy((1.0 / shot.vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    out = []
+    for store in (False, True):
+        geo = adjoint.Geometry.from_shot(shot, checkpoint_every=25, sponge_vmax=3200.0, store_all=store)
+        J, g = adjoint.misfit_and_gradient(m, geo, dobs)
+        out.append((J, g.cpu().numpy()))
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
