@@ -325,3 +325,24 @@ def test_store_all_gradient_equals_checkpointed(fdlib, ndim):
         out.append((J, g.cpu().numpy()))
     assert out[0][0] == out[1][0]
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_store_all_entry_points_check_arguments(fdlib):
+    import torch
+    shape = (21, 17, 29)
+    shot = _segment_case(fdlib, shape, seed=6)
+    lp = torch.zeros((3,) + shape, device="cuda")
+    grad = torch.zeros(shape, device="cuda")
+    g = torch.zeros((3, len(shot.receivers)), device="cuda")
+    with fdlib.Model.from_shot(shot) as fwd, fdlib.Model.from_shot(shot) as adj:
+        fdlib.fd_step_lp_n(fwd.handle, 0, lp)                     # zero steps: nothing to do
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_step_lp_n(fwd.handle, -1, lp)
+        assert e.value.status == -1
+        fdlib.fd_step_lp_n(fwd.handle, 3, lp)
+        assert fdlib.fd_get_step(fwd.handle) == 3
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_adjoint_backward(adj.handle, 2, 2, lp, g, grad)
+        assert e.value.status == -1
+        fdlib.fd_adjoint_backward(adj.handle, 0, 3, lp, g, grad)
+        assert fdlib.fd_get_step(adj.handle) == 3
