@@ -376,3 +376,35 @@ def test_parity_3d_long_run_2000_steps(fdlib, oracle):
     FP32 rounding from growing into a spurious mass term)."""
     shot = wl.roofline_3d(n=64, nt=2000, sponge_width=10)
     assert_parity(gpu_run(fdlib, shot, shot.nt), oracle_run(oracle, shot, shot.nt), "3d 64 long run")
+
+
+@pytest.mark.parametrize("shape", [(64, 96), (40, 44, 52)])
+@pytest.mark.parametrize("sponge", [0, 6])
+def test_gpu_discrete_energy(fdlib, shape, sponge):
+    """An oracle-free property of the GPU step: with no source, the discrete energy
+    E^(n+1/2) = sum (Pn - P)^2 / w - sum Pn L'P (FP64 from the FP32 levels) is
+    constant to FP32 rounding over 2000 steps without a sponge, and never grows
+    with one.  It holds only for a symmetric stencil under the zero halo."""
+    ndim = len(shape)
+    h = 10.0
+    v = wl.grf_velocity(shape, corr_cells=4.0, vmin=1500.0, vmax=3000.0, seed=12)
+    dt = 0.4 * h / float(v.max())
+    f = wl.random_field(shape, 3.0, 13)
+    P0 = (f / f.std()).astype(np.float32)
+    Pm1 = (np.roll(f, 1, axis=-1) / f.std()).astype(np.float32)
+    c = pl.fornberg_coefficients(4)
+    w = (dt * v.astype(np.float64) / h) ** 2
+    E = []
+    with fdlib.Model(ndim, shape, h, dt, v, sponge) as m:
+        fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
+        for _ in range(20):
+            fdlib.fd_step(m.handle, 100)
+            P, Pold = m.wavefield(with_old=True)
+            E.append(pl.energy(Pold.astype(np.float64), P.astype(np.float64), w, c))
+    E = np.array(E)
+    assert np.all(E > 0)
+    if sponge == 0:
+        assert np.max(np.abs(E - E[0])) / E[0] < 1e-4, E
+    else:
+        assert np.all(np.diff(E) <= 1e-6 * E[0]), E
+        assert E[-1] < 0.5 * E[0]
