@@ -107,3 +107,20 @@ def test_no_device_is_ecuda(fdlib):
     with pytest.raises(fdlib.FDError) as e:
         fdlib.fd_model_create(_desc(fdlib), np.full(16 * 12, 2000.0, np.float32))
     assert e.value.status in (fdlib.FD_ECUDA, fdlib.FD_ENOMEM)
+
+
+def _build_c_example(tmp_path):
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2311_05038_b300")
+    exe = str(tmp_path / "example_shot")
+    cmd = ["gcc", "-O2", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+           os.path.join(pkg, "csrc", "example_shot.c"), "-L", pkg, "-lfd", f"-Wl,-rpath,{pkg}", "-lm", "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_c_example_compiles_and_links_against_the_header_alone(fdlib, tmp_path):
+    """A C caller needs only include/fd.h and libfd.so (no Python, no torch)."""
+    assert os.path.exists(_build_c_example(tmp_path))
