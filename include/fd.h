@@ -180,10 +180,13 @@ fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
  * adjoint of fd_step for dJ/dtrace^n = g^n is the same step run backwards in
  * time on psi (a model with the same velocity and no source), with
  * w g^{k-1} / (1 + a) added at the receivers after step k (fd_inject_receivers),
- * and dJ/dm = -(1/m) sum_n psi_{n+1} (L' P^n), accumulated either by
- * fd_imaging (which evaluates L' from a stored P^n) or, cheaper, by
- * fd_imaging_product from the L'P^n that fd_step_lp writes while the forward
- * segment is recomputed; fd_adjoint_segment runs a whole checkpoint segment. */
+ * and dJ/dm = -(1/m) sum_n psi_{n+1} (L' P^n).  The gradient is accumulated by
+ * fd_imaging (which evaluates L' from a stored P^n), by fd_imaging_product from
+ * the L'P^n that fd_step_lp writes while the forward segment is recomputed, or,
+ * cheapest, inside the adjoint step itself (fd_step_image with
+ * fd_inject_receivers_image).  fd_adjoint_segment runs a whole checkpoint
+ * segment; fd_step_lp_n and fd_adjoint_backward serve a run that keeps every
+ * L'P^n instead of checkpoints. */
 
 /* Copy P (level n) and, if pold_dev is not NULL, Pold to dense device arrays
  * [nz][ny][nx] (asynchronous on the model's stream). */
