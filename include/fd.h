@@ -353,6 +353,15 @@ fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels, int nsteps
  * when nx is a multiple of 32. */
 fd_status fd_debug_poison_padding(fd_model *m);
 
+/* Test hook for the step kernel's failure path: while stage >= 0, the first CTA
+ * of every 3D step launch never issues the TMA load of its two-plane P stage
+ * `stage` (counted from its first halo plane), so that CTA's bounded waits run
+ * out (about 2 s): the kernel raises the device error word, its other CTAs
+ * finish, and fd_synchronize returns FD_ETIMEOUT with the context still usable.
+ * The wavefield is undefined afterwards until reset.  -1 clears the hook.
+ * 2D models ignore it. */
+fd_status fd_debug_stall_stage(fd_model *m, int stage);
+
 /* Number of CUDA kernel launches this library has issued since load. */
 uint64_t fd_kernel_launch_count(void);
 

@@ -603,6 +603,7 @@ static fd_status step_n(fd_model *m, int nsteps, float *lp, const float *img_lp 
                         float *img_grad = nullptr)
 {
     StepParams p{};
+    p.stall_stage = m->stall_stage;
     p.lp_out = lp;
     p.img_lp = img_lp;
     p.img_grad = img_grad;
@@ -700,6 +701,15 @@ extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
     if (st)
         return st;
     return fd_step(m, nt);
+}
+
+extern "C" fd_status fd_debug_stall_stage(fd_model *m, int stage)
+{
+    NEED_MODEL(m);
+    if (stage < -1)
+        return fail(FD_EINVAL, "fd_debug_stall_stage: stage must be >= -1");
+    m->stall_stage = stage;
+    return FD_OK;
 }
 
 extern "C" fd_status fd_debug_poison_padding(fd_model *m)

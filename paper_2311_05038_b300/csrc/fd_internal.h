@@ -72,6 +72,7 @@ struct StepParams {
     const float *img_lp;      // if set (adjoint imaging launches): img_grad += Pn * img_lp,
     float *img_grad;          //   both dense [nz][ny][nx]
     int *err;                 // device error word
+    int stall_stage = -1;     // test hook: CTA (0, 0) of the 3D step never issues this P stage (-1: none)
 };
 
 size_t step3d_smem_bytes();

@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const int lane = tid & 31;
 
     auto issueP = [&](int k, int slot) {
+        if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
+            return;   // test hook: the stage never arrives, so this CTA's bounded waits run out
         mbar_arrive_expect_tx(&fullP[slot], BYTES_P);
         tma_load_3d(sP + slot * PST, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + 2 * k);
         atomicAdd(&s_issuedP, 1);

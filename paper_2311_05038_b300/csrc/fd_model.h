@@ -55,6 +55,7 @@ struct fd_model {
     size_t trace_cap = 0;      // floats in an owned trace buffer
     float *stage = nullptr;    // velocity staging, kept once fd_set_velocity is used
 
+    int stall_stage = -1;     // fd_debug_stall_stage
     int n = 0;
     int pending_row = -1;      // receiver row whose gather is still owed
 

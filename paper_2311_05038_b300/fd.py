@@ -42,7 +42,7 @@ EXPORTS = [
     "fd_get_wavefield_dev", "fd_set_wavefield_dev", "fd_inject_receivers", "fd_imaging",
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
     "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
-    "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward",
+    "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward", "fd_debug_stall_stage",
 ]
 
 
@@ -93,6 +93,7 @@ _SIGS = {
     "fd_gather_traces": (_i, [_vp, _vp, _sz]),
     "fd_gather_traces_async": (_i, [_vp, _vp, _sz]),
     "fd_debug_poison_padding": (_i, [_vp]),
+    "fd_debug_stall_stage": (_i, [_vp, _i]),
     "fd_step_image": (_i, [_vp, _vp, _vp]),
     "fd_inject_receivers_image": (_i, [_vp, _vp, _vp, _vp]),
     "fd_step_lp_n": (_i, [_vp, _i, _vp]),
@@ -274,6 +275,11 @@ def fd_get_wavefield(m: int, shape, with_old: bool = False):
     _check(_lib.fd_get_wavefield(m, p.ctypes.data, None if po is None else po.ctypes.data, n),
            "fd_get_wavefield")
     return (p, po) if with_old else p
+
+
+def fd_debug_stall_stage(m: int, stage: int):
+    """Test hook: the first CTA of each 3D step launch never issues P stage `stage` (-1 clears)."""
+    _check(_lib.fd_debug_stall_stage(m, int(stage)), "fd_debug_stall_stage")
 
 
 def fd_debug_poison_padding(m: int):

@@ -408,3 +408,28 @@ def test_gpu_discrete_energy(fdlib, shape, sponge):
     else:
         assert np.all(np.diff(E) <= 1e-6 * E[0]), E
         assert E[-1] < 0.5 * E[0]
+
+
+@pytest.mark.parametrize("stage", [0, 6])
+def test_step_kernel_wait_times_out_and_context_survives(fdlib, oracle, stage):
+    """A P stage that never arrives (the test hook keeps the first CTA from issuing
+    it: an initial stage, or a refill) runs that CTA's bounded waits out: the next
+    synchronisation reports FD_ETIMEOUT within seconds, and a clean run on the same
+    model then matches the oracle.  Nothing faults, traps or hangs."""
+    import time
+    shot = wl.roofline_3d(shape=(40, 36, 70), nt=30, sponge_width=6)
+    with fdlib.Model.from_shot(shot) as m:
+        fdlib.fd_debug_stall_stage(m.handle, stage)
+        t0 = time.perf_counter()
+        fdlib.fd_step(m.handle, 1)
+        with pytest.raises(fdlib.FDError) as e:
+            fdlib.fd_synchronize(m.handle)
+        assert e.value.status == -7                      # FD_ETIMEOUT
+        assert time.perf_counter() - t0 < 30
+        fdlib.fd_debug_stall_stage(m.handle, -1)
+        fdlib.fd_reset(m.handle)
+        fdlib.fd_set_trace_buffer(m.handle, None, shot.nt)
+        fdlib.fd_step(m.handle, shot.nt)
+        tr = m.traces(shot.nt)
+        P, Pold = m.wavefield(with_old=True)
+    assert_parity((P, Pold, tr), oracle_run(oracle, shot, shot.nt), f"after a timeout at stage {stage}")
