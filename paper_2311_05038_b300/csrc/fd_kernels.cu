@@ -51,7 +51,8 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 //
 // MODE 1 also writes L'P (the stencil sum of level n) to the dense array
 // prm.lp_out; MODE 2 also adds Pn * prm.img_lp to prm.img_grad.  Both serve the
-// adjoint's imaging condition; MODE 0 is the plain step.
+// adjoint's imaging condition; MODE 0 is the plain step.  MODE 3 is the plain
+// step with the failure-path test hook (prm.stall_stage), kept out of MODE 0.
 template <int TX, int TY, int SP, int ST, int G, int MODE>
 __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
@@ -97,8 +98,10 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const int lane = tid & 31;
 
     auto issueP = [&](int k, int slot) {
-        if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
-            return;   // test hook: the stage never arrives, so this CTA's bounded waits run out
+        if constexpr (MODE == 3) {
+            if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
+                return;   // test hook: the stage never arrives, so this CTA's bounded waits run out
+        }
         mbar_arrive_expect_tx(&fullP[slot], BYTES_P);
         tma_load_3d(sP + slot * PST, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + 2 * k);
         atomicAdd(&s_issuedP, 1);
@@ -480,6 +483,8 @@ cudaError_t step3d_prepare()
         e = cudaFuncSetAttribute(FD_STEP3D(1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(FD_STEP3D(2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(3), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
@@ -501,6 +506,8 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
         FD_STEP3D(1)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     else if (p.img_grad)
         FD_STEP3D(2)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else if (p.stall_stage >= 0)
+        FD_STEP3D(3)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     else
         FD_STEP3D(0)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     return cudaGetLastError();
