@@ -104,6 +104,25 @@ fd_status fd_model_create_dev(const fd_grid_desc *desc, const float *v_dev, void
 /* Release everything the model owns (waits for its stream first).  NULL is a no-op. */
 fd_status fd_model_destroy(fd_model *m);
 
+/* Move the model's later GPU work to another stream (a cudaStream_t of the
+ * model's device; NULL = the legacy default stream).  Work already enqueued
+ * keeps its order: the library records an event on the old stream and makes
+ * the new stream wait for it before anything the model enqueues later.  The
+ * caller keeps the new stream alive until the model is destroyed or moved
+ * again.  Not part of the paper's interface: a serving loop uses it to change
+ * a shot's stream priority while the shot is running.  Errors: FD_EINVAL,
+ * FD_ECUDA. */
+fd_status fd_set_stream(fd_model *m, void *stream);
+
+/* A non-blocking stream of the current device with the given priority (lower
+ * numbers are scheduled first; values outside the device's range are clamped
+ * to it), owned by the caller until fd_stream_destroy.  *greatest, if not NULL,
+ * receives the device's highest priority (a negative number on current GPUs;
+ * 0 is the default priority).  Errors: FD_EINVAL, FD_ECUDA. */
+fd_status fd_stream_create(int priority, void **stream, int *greatest);
+/* Destroy a stream from fd_stream_create (work already enqueued still runs). */
+fd_status fd_stream_destroy(void *stream);
+
 /* Replace the velocity model (same grid and dt); recomputes w and the sponge.
  * Same checks as create (FD_EINVAL, FD_ECFL).  Does not touch P, Pold or n. */
 fd_status fd_set_velocity(fd_model *m, const float *v_host);
@@ -337,11 +356,16 @@ fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best)
  * at most 64 models, 32768 tiles of 64 x 16 points in total and 32768
  * receivers in total; larger requests return FD_EBUDGET and change nothing.
  * The first call on a device looks up the array's device address and sets the
- * kernel's shared-memory limit, so make that first call before any stream
- * capture.  Every call shares the array and leaves its tables there; the call
- * clears the counters, launch state and error word it uses before launching.
- * Calls that overlap on the GPU (from several host threads, or processes
- * sharing a context) race on the array and must be serialised by the caller.
+ * kernel's shared-memory limit; the address is cached per device for the life
+ * of the process, which assumes the device's primary context is never reset
+ * (after cudaDeviceReset the cache is stale).  Every call synchronises the
+ * models' streams and reads the error word back synchronously, so no call may
+ * be made inside a stream capture, nor while another thread captures in
+ * global mode.  Every call shares the array and leaves its tables there; the
+ * call clears the counters, launch state and error word it uses before
+ * launching.  Calls hold a process-wide lock until their kernel has finished,
+ * so two calls of one process never overlap on the GPU; two processes have
+ * separate arrays.  Host work per call is O(models + tiles + receivers).
  * Errors as fd_batch_step (FD_EINVAL, FD_EBUDGET, FD_ECUDA, FD_ETIMEOUT). */
 fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels, int nsteps);
 

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -831,8 +832,10 @@ struct NoAllocScratch {
 };
 
 NoAllocScratch h_noalloc;                           // host staging of the tables
+int h_noalloc_cursor[kNoAllocMaxItems];             // per-tile receiver counts, then write cursors
 void *g_noalloc_addr[kNoAllocMaxDevices] = {};      // device address of the array, per device
 bool g_noalloc_ready[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;                         // one call at a time per process
 
 }  // namespace
 
@@ -871,6 +874,9 @@ extern "C" fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels,
     const int dev = models[0]->device;
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(FD_EINVAL, "fd_batch_step_noalloc: device %d out of range", dev);
+    // The host staging buffer, the address cache and the device array are shared:
+    // the lock is held until the kernel has finished, so calls never overlap.
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     FD_CUDA(cudaSetDevice(dev), "cudaSetDevice");
 
     // One-time set-up on this device (the device is current): the device
@@ -928,15 +934,31 @@ extern "C" fd_status fd_batch_step_noalloc(fd_model *const *models, int nmodels,
             it.nb[1] = tx + 1 < tx_n ? base + t + 1 : -1;
             it.nb[2] = tz > 0 ? base + t - tx_n : -1;
             it.nb[3] = tz + 1 < tz_n ? base + t + tx_n : -1;
+        }
+        // receivers bucketed by tile (a counting sort, O(nrec + tiles)); within a
+        // tile they stay in receiver order
+        int *cur = h_noalloc_cursor;
+        const int ntile = tx_n * tz_n;
+        for (int t = 0; t < ntile; ++t)
+            cur[t] = 0;
+        auto tile_of = [&](int r) {
+            const int64_t di = m->rec_dense[r];
+            const int ix = (int)(di % m->nx), iz = (int)(di / m->nx);
+            return (iz / v.tz) * tx_n + ix / v.tx;
+        };
+        for (int r = 0; r < m->nrec; ++r)
+            ++cur[tile_of(r)];
+        for (int t = 0; t < tx_n * tz_n; ++t) {
+            BatchItem &it = h.items[base + t];
             it.rec_begin = nr;
-            // receivers of this tile, in receiver order
-            for (int r = 0; r < m->nrec; ++r) {
-                const int64_t di = m->rec_dense[r];
-                const int ix = (int)(di % m->nx), iz = (int)(di / m->nx);
-                if (ix / v.tx == tx && iz / v.tz == tz)
-                    h.recs[nr++] = BatchRec{(iz % v.tz) * v.tx + ix % v.tx, r};
-            }
+            nr += cur[t];
             it.rec_end = nr;
+            cur[t] = it.rec_begin;
+        }
+        for (int r = 0; r < m->nrec; ++r) {
+            const int64_t di = m->rec_dense[r];
+            const int ix = (int)(di % m->nx), iz = (int)(di / m->nx);
+            h.recs[cur[tile_of(r)]++] = BatchRec{(iz % v.tz) * v.tx + ix % v.tx, r};
         }
         ni += tx_n * tz_n;
     }

@@ -73,6 +73,40 @@ def test_no_alloc_matches_batch_step_on_two_calls(fdlib):
         m.close()
 
 
+def test_no_alloc_second_call_on_other_models_ignores_leftovers(fdlib, oracle):
+    """One call on three models leaves its descriptors, tile table and receiver
+    lists in the shared array; a following call on two other models, with other
+    grids, receiver counts and sponge settings, must match both the allocating
+    batch entry point and the oracle."""
+    nt = 60
+    first = shots(n=3, nt=nt, seed=71)
+    models = fresh_models(fdlib, first, nt)
+    fdlib.fd_batch_step_noalloc([m.handle for m in models], nt)
+    for m in models:
+        m.close()
+    second = []
+    for i, (nz, nx, W) in enumerate(((37, 91, 0), (70, 45, 5))):
+        vel = wl.grf_velocity((nz, nx), corr_cells=4.0, vmin=1500.0, vmax=3500.0, seed=90 + i)
+        dt = wl.courant_dt(10.0, float(vel.max()))
+        rec = np.array([(ix, 0, iz) for iz in (3, nz - 4) for ix in range(1, nx, 7 + i)], np.int32)
+        second.append(wl.Shot(2, (nz, nx), 10.0, dt, nt, vel, (nx // 3, 0, nz // 2), wl.ricker(nt, dt, 30.0), rec,
+                              sponge_width=W))
+    ref_models = fresh_models(fdlib, second, nt)
+    with fdlib.Batch(ref_models) as b:
+        b.step(nt)
+        ref = state(ref_models, nt)
+    models = fresh_models(fdlib, second, nt)
+    fdlib.fd_batch_step_noalloc([m.handle for m in models], nt)
+    got = state(models, nt)
+    assert_close(got, ref)
+    for s, ((P, Po), tr) in zip(second, got):
+        Pr, Por, trr = oracle.run(2, s.shape, s.h, s.dt, s.vel, sponge_width=s.sponge_width, src=s.src,
+                                  wavelet=s.wavelet, receivers=s.receivers, nsteps=nt)
+        assert pl.rel_l2(P, Pr) <= TOL and pl.rel_l2(Po, Por) <= TOL and pl.rel_l2(tr, trr) <= TOL
+    for m in models + ref_models:
+        m.close()
+
+
 def test_no_alloc_rejects_requests_beyond_its_limits(fdlib):
     ss = shots(n=1, nt=4)
     with fdlib.Model.from_shot(ss[0]) as m:
