@@ -99,8 +99,12 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
 
     auto issueP = [&](int k, int slot) {
         if constexpr (MODE == 3) {
-            if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
-                return;   // test hook: the stage never arrives, so this CTA's bounded waits run out
+            if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0) {
+                // test hook: the stage is counted as issued but never loaded, so this
+                // CTA's bounded waits run out; the drain below skips it
+                atomicAdd(&s_issuedP, 1);
+                return;
+            }
         }
         mbar_arrive_expect_tx(&fullP[slot], BYTES_P);
         tma_load_3d(sP + slot * PST, &tmP, &fullP[slot], x0 - 4, y0 - 4, z0 - 4 + 2 * k);
@@ -339,8 +343,15 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     __syncthreads();
     if (tid == 0 && s_abort) {
         int never = 0;
-        for (int k = max(0, s_issuedP - SP); k < s_issuedP; ++k)
+        // the issued stages are always 0 .. s_issuedP-1: stage k+SP is issued only
+        // after every warp has freed stage k
+        for (int k = max(0, s_issuedP - SP); k < s_issuedP; ++k) {
+            if constexpr (MODE == 3) {
+                if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
+                    continue;   // withheld by the test hook: nothing in flight
+            }
             mbar_wait(&fullP[k % SP], (k / SP) & 1, &never, kWaitLimitCycles / 8);
+        }
         for (int t = max(0, s_issuedT - ST); t < s_issuedT; ++t)
             mbar_wait(&fullT[t % ST], (t / ST) & 1, &never, kWaitLimitCycles / 8);
     }
