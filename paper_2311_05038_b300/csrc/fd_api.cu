@@ -209,6 +209,8 @@ static void free_model(fd_model *m)
         cudaFree(d);
     if (m->traces_owned)
         cudaFree(m->traces);
+    if (m->handoff)
+        cudaEventDestroy(m->handoff);
     delete m;
 }
 
@@ -701,6 +703,44 @@ extern "C" fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev)
     if (st)
         return st;
     return fd_step(m, nt);
+}
+
+extern "C" fd_status fd_set_stream(fd_model *m, void *stream)
+{
+    NEED_MODEL(m);
+    cudaStream_t to = static_cast<cudaStream_t>(stream);
+    if (to == m->stream)
+        return FD_OK;
+    if (!m->handoff)
+        FD_CUDA(cudaEventCreateWithFlags(&m->handoff, cudaEventDisableTiming), "cudaEventCreate");
+    FD_CUDA(cudaEventRecord(m->handoff, m->stream), "cudaEventRecord");
+    FD_CUDA(cudaStreamWaitEvent(to, m->handoff, 0), "cudaStreamWaitEvent");
+    m->stream = to;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_stream_create(int priority, void **stream, int *greatest)
+{
+    if (!stream)
+        return fail(FD_EINVAL, "fd_stream_create: NULL output");
+    *stream = nullptr;
+    int least = 0, most = 0;
+    FD_CUDA(cudaDeviceGetStreamPriorityRange(&least, &most), "cudaDeviceGetStreamPriorityRange");
+    const int p = std::min(least, std::max(most, priority));
+    cudaStream_t s = nullptr;
+    FD_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, p), "cudaStreamCreateWithPriority");
+    *stream = s;
+    if (greatest)
+        *greatest = most;
+    return FD_OK;
+}
+
+extern "C" fd_status fd_stream_destroy(void *stream)
+{
+    if (!stream)
+        return fail(FD_EINVAL, "fd_stream_destroy: NULL stream");
+    FD_CUDA(cudaStreamDestroy(static_cast<cudaStream_t>(stream)), "cudaStreamDestroy");
+    return FD_OK;
 }
 
 extern "C" fd_status fd_debug_stall_stage(fd_model *m, int stage)

@@ -22,6 +22,7 @@ struct fd_model {
     size_t npts = 0;       // nz * ny * nx
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t handoff = nullptr;   // fd_set_stream: orders the new stream after the old one
 
     float *buf[2] = {nullptr, nullptr};   // the two wavefield levels
     int cur = 0;                          // buf[cur] = P, buf[cur ^ 1] = Pold

@@ -43,6 +43,7 @@ EXPORTS = [
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
     "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
     "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward", "fd_debug_stall_stage",
+    "fd_set_stream", "fd_stream_create", "fd_stream_destroy",
 ]
 
 
@@ -123,6 +124,9 @@ _SIGS = {
     "fd_set_sponge_vmax": (_i, [_vp, ctypes.c_double]),
     "fd_batch_set_fault": (_i, [_vp, _i]),
     "fd_step_unfused": (_i, [_vp, _i]),
+    "fd_set_stream": (_i, [_vp, _vp]),
+    "fd_stream_create": (_i, [_i, ctypes.POINTER(_vp), _ip]),
+    "fd_stream_destroy": (_i, [_vp]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -193,6 +197,22 @@ def fd_model_create_dev(desc: fd_grid_desc, v_dev, stream=None) -> int:
 
 def fd_model_destroy(m: int):
     _check(_lib.fd_model_destroy(m), "fd_model_destroy")
+
+
+def fd_set_stream(m: int, stream):
+    _check(_lib.fd_set_stream(m, _stream_ptr(stream)), "fd_set_stream")
+
+
+def fd_stream_create(priority: int = 0):
+    """(stream handle, device's greatest priority) of a new library-owned stream."""
+    out = _vp()
+    most = ctypes.c_int(0)
+    _check(_lib.fd_stream_create(int(priority), ctypes.byref(out), ctypes.byref(most)), "fd_stream_create")
+    return out.value, most.value
+
+
+def fd_stream_destroy(stream: int):
+    _check(_lib.fd_stream_destroy(stream), "fd_stream_destroy")
 
 
 def fd_set_velocity(m: int, v_host, n=None):

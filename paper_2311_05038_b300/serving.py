@@ -4,10 +4,23 @@ A request is one shot (grid, velocity, source, receivers, step count) with an
 arrival time.  The server keeps a set of active shots whose wavefields stay
 resident on the device; each advances on a CUDA stream of its own, in chunks of
 time steps (``fd_step``), with up to ``depth`` chunks queued, so the kernels of
-several shots run on the GPU at the same time.  Requests that arrive while
-others run wait in a FIFO queue and are admitted as soon as a slot is free and
-their device memory fits the HBM budget.  When a shot's last chunk completes,
-its traces are read back and its model returns to a pool.
+several shots run on the GPU at the same time.  When a shot's last chunk
+completes, its traces are read back and its model returns to a pool.
+
+Admission.  Requests that arrive while others run wait in arrival order and are
+admitted as soon as a slot is free and their device memory fits the HBM budget.
+A request that does not fit yet lets later requests that do fit pass it, at
+most ``max_bypass`` times; after that nothing passes it until it is admitted,
+so no request starves.
+
+Priorities.  Overlap alone shares the GPU evenly between the active shots,
+which stretches the longest shots and so the latency tail.  Each active shot's
+stream therefore carries a priority: the oldest active request the highest,
+the others ordered by their remaining work (shortest first), so the block
+scheduler gives the head of the queue the SMs it can use and fills the rest
+(tail waves, gaps between launches, small grids) with the others' blocks.  A
+shot changes priority by moving to another stream of its own
+(``fd_set_stream``, which keeps its work in order).
 
 Models are pooled per grid and reused for later requests of the same grid
 instead of being freed: ``cudaFree`` synchronises the whole device and would
@@ -136,8 +149,12 @@ class _Active:
     model: object
     key: tuple
     admitted: float
-    remaining: int
-    inflight: collections.deque = field(default_factory=collections.deque)
+    remaining: int              # steps not yet issued
+    inflight: collections.deque = field(default_factory=collections.deque)   # (event, steps)
+
+    def work_left(self) -> int:
+        """Grid-point updates not yet completed."""
+        return (self.remaining + sum(k for _, k in self.inflight)) * int(self.req.shot.npoints)
 
 
 class Server:
@@ -148,25 +165,51 @@ class Server:
     chunk       time steps per fd_step call; depth: chunks queued per shot
     max_nt      largest step count a request may ask for (trace buffers are
                 sized for it once per pooled model)
+    priorities  give the oldest active shot the highest stream priority and the
+                others priorities by remaining work (default: on when more than
+                one shot may be active)
+    max_bypass  how many later requests may be admitted ahead of a waiting
+                request that does not fit yet
     """
 
-    def __init__(self, max_active=8, budget_bytes=150 * 10**9, chunk=100, depth=2, max_nt=2000):
+    def __init__(self, max_active=8, budget_bytes=150 * 10**9, chunk=100, depth=2, max_nt=2000,
+                 priorities=None, max_bypass=8):
         import torch
         self.torch = torch
         self.max_active = int(max_active)
         self.chunk = int(chunk)
         self.depth = int(depth)
         self.max_nt = int(max_nt)
+        self.priorities = self.max_active > 1 if priorities is None else bool(priorities)
+        self.max_bypass = int(max_bypass)
+        self.greatest = None             # the device's highest stream priority, once known
         self.pool = ModelPool(budget_bytes, self._create, self._destroy)
+
+    # -- streams: each pooled model owns one library stream per priority it has used
+    def _stream(self, m, prio):
+        if prio not in m.streams:
+            handle, greatest = fd.fd_stream_create(prio)
+            self.greatest = greatest
+            m.streams[prio] = (handle, self.torch.cuda.ExternalStream(handle))
+        return m.streams[prio]
+
+    def _set_priority(self, m, prio):
+        if m.prio != prio:
+            handle, _ = self._stream(m, prio)
+            fd.fd_set_stream(m.handle, handle)
+            m.prio = prio
 
     # -- pool callbacks
     def _create(self, key):
         shape, h, dt, W, R, nrec, max_nt = key
-        stream = self.torch.cuda.Stream()
-        nz, ny, nx = shape
         vel = np.full(shape, 1500.0, np.float32)
-        m = fd.Model(3, shape, h, dt, vel, W, R, stream=stream)
-        m.stream = stream
+        streams = {}
+        handle, greatest = fd.fd_stream_create(0)
+        self.greatest = greatest
+        streams[0] = (handle, self.torch.cuda.ExternalStream(handle))
+        m = fd.Model(3, shape, h, dt, vel, W, R, stream=handle)
+        m.streams = streams
+        m.prio = 0
         # reserve the per-request buffers once: receivers, source signature, traces
         m.set_receivers(np.zeros((nrec, 3), np.int32))
         m.set_source((0, 0, 0), np.zeros(max_nt, np.float32))
@@ -174,7 +217,10 @@ class Server:
         return m
 
     def _destroy(self, m):
-        m.close()
+        m.close()                       # waits for the model's current stream, which is ordered last
+        for handle, _ in m.streams.values():
+            fd.fd_stream_destroy(handle)
+        m.streams = {}
 
     # -- one request
     def _admit(self, req: Request, now: float):
@@ -195,14 +241,26 @@ class Server:
         fd.fd_set_trace_buffer(m.handle, None, shot.nt)
         return _Active(req, m, key, now, shot.nt)
 
+    def _reprioritise(self, active):
+        """Oldest request first, then shortest remaining work; priorities from the
+        device's greatest down to 0 (the default), the rest at 0."""
+        if not self.priorities or not active:
+            return
+        oldest = min(active, key=lambda a: (a.req.arrival, a.req.rid))
+        rest = sorted((a for a in active if a is not oldest), key=lambda a: (a.work_left(), a.req.rid))
+        top = self.greatest if self.greatest is not None else 0
+        for i, a in enumerate([oldest] + rest):
+            self._set_priority(a.model, min(0, top + i))
+
     def serve(self, requests, realtime=True):
         """Serve the requests (arrival times relative to the call); returns the
         results in request order.  With realtime=False every request is treated as
         arrived at the start (closed loop), and latencies count from there."""
         torch = self.torch
-        reqs = sorted(requests, key=lambda r: r.arrival)
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         pending = collections.deque(reqs)
-        waiting = collections.deque()
+        waiting = []                      # arrived, not admitted, in arrival order
+        bypassed = 0                      # admissions ahead of waiting[0]
         active = []
         results = {}
         t0 = time.perf_counter()
@@ -211,24 +269,32 @@ class Server:
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             progressed = False
-            while waiting and len(active) < self.max_active:
-                a = self._admit(waiting[0], now)
-                if a is None:
+            i = 0
+            while i < len(waiting) and len(active) < self.max_active:
+                if i > 0 and bypassed >= self.max_bypass:
                     break
-                waiting.popleft()
+                a = self._admit(waiting[i], now)
+                if a is None:             # does not fit yet: later requests may pass it
+                    i += 1
+                    continue
+                del waiting[i]
+                bypassed = bypassed + 1 if i > 0 else 0
                 active.append(a)
                 progressed = True
+            if progressed:
+                self._reprioritise(active)
             for a in active:
                 while a.remaining > 0 and len(a.inflight) < self.depth:
                     k = min(self.chunk, a.remaining)
                     fd.fd_step(a.model.handle, k)
                     ev = torch.cuda.Event()
-                    ev.record(a.model.stream)
-                    a.inflight.append(ev)
+                    ev.record(a.model.streams[a.model.prio][1])
+                    a.inflight.append((ev, k))
                     a.remaining -= k
                     progressed = True
+            finished = False
             for a in list(active):
-                while a.inflight and a.inflight[0].query():
+                while a.inflight and a.inflight[0][0].query():
                     a.inflight.popleft()
                     progressed = True
                 if a.remaining == 0 and not a.inflight:
@@ -240,7 +306,9 @@ class Server:
                                                 int(a.req.shot.npoints) * nt)
                     self.pool.release(a.key, a.model)
                     active.remove(a)
-                    progressed = True
+                    progressed = finished = True
+            if finished:
+                self._reprioritise(active)
             if not progressed:
                 if active:
                     time.sleep(2e-5)

@@ -100,6 +100,9 @@ def test_null_arguments_are_einval(fdlib):
     assert fdlib._lib.fd_gather_traces(None, None, 0) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_stencil_weights(None) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_model_destroy(None) == fdlib.FD_OK
+    assert fdlib._lib.fd_set_stream(None, None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_stream_create(0, None, None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_stream_destroy(None) == fdlib.FD_EINVAL
 
 
 @pytest.mark.skipif(cuda_available(), reason="checks the no-device error path")
