@@ -6,6 +6,8 @@ host.  Floating-point results must match the oracle within a relative L2
 error of 1e-4 (wavefield and traces); integer maps (source and receiver
 indices, sponge band extents) must match exactly.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -433,3 +435,46 @@ def test_step_kernel_wait_times_out_and_context_survives(fdlib, oracle, stage):
         tr = m.traces(shot.nt)
         P, Pold = m.wavefield(with_old=True)
     assert_parity((P, Pold, tr), oracle_run(oracle, shot, shot.nt), f"after a timeout at stage {stage}")
+
+
+# ------------------------------------------------------------ full benchmark shot
+
+GOLDEN_ROOFLINE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                               "roofline_3d_512_1000steps_oracle.npz")
+
+
+def test_parity_3d_roofline_full_run(fdlib):
+    """The benchmark's shot (512^3 layered, sponge 20, 10 Hz source, 65 536 receivers)
+    over all 1000 steps through fd_run_shot, against the FP64 oracle's run of the
+    same inputs (section 7, Eq. 1).
+
+    The oracle's outputs are stored as a digest written by
+    tests/golden/make_roofline_3d_digest.py, which calls only the oracle.  Checks:
+    element by element on the final P over the vertical plane through the source
+    and on the traces of the receiver row through the source (rel L2 <= 1e-4),
+    and over the WHOLE final P, Pold and trace array through their CountSketches,
+    whose difference estimates the full rel L2 to about 1 % of itself (bar 1e-4).
+    """
+    import digest
+    ref = np.load(GOLDEN_ROOFLINE)
+    shot = wl.roofline_3d(n=512, nt=1000)
+    assert str(ref["name"]) == shot.name and tuple(ref["shape"]) == shot.shape
+    P, Pold, tr = gpu_run(fdlib, shot, shot.nt)
+    assert np.all(np.isfinite(P)) and np.all(np.isfinite(Pold)) and np.all(np.isfinite(tr))
+    iy = int(ref["plane_iy"])
+    row = ref["row_receivers"]
+    e_plane = pl.rel_l2(P[:, iy, :], ref["plane_P"])
+    e_row = pl.rel_l2(tr[:, row], ref["row_traces"])
+    k, seed = int(ref["sketch_k"]), int(ref["sketch_seed"])
+    (nP, nO), (yP, yO) = digest.sketch([P, Pold], k, seed)
+    (nT,), (yT,) = digest.sketch([tr], k, seed)
+    e_P = digest.sketch_rel_l2(yP, ref["sketch_P"], float(ref["norm_P"]))
+    e_O = digest.sketch_rel_l2(yO, ref["sketch_Pold"], float(ref["norm_Pold"]))
+    e_T = digest.sketch_rel_l2(yT, ref["sketch_traces"], float(ref["norm_traces"]))
+    print(f"512^3 x 1000 vs oracle: plane {e_plane:.2e}, receiver row {e_row:.2e}; "
+          f"whole P {e_P:.2e}, Pold {e_O:.2e}, traces {e_T:.2e} (sketch estimates); "
+          f"norms {nP / float(ref['norm_P']) - 1:+.1e} {nO / float(ref['norm_Pold']) - 1:+.1e} "
+          f"{nT / float(ref['norm_traces']) - 1:+.1e}")
+    assert max(e_plane, e_row, e_P, e_O, e_T) <= TOL, (e_plane, e_row, e_P, e_O, e_T)
+    for got, key in ((nP, "norm_P"), (nO, "norm_Pold"), (nT, "norm_traces")):
+        assert abs(got / float(ref[key]) - 1.0) <= TOL, key
