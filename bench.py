@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--adjoint-shots", type=int, default=8, help="adjoint workload: shots per gradient")
-    ap.add_argument("--serve-shots", type=int, default=48, help="serving workload: requests in the stream")
+    ap.add_argument("--serve-shots", type=int, default=500, help="serving workload: requests in the stream")
     ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
     ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
@@ -315,12 +315,13 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
 
 # ------------------------------------------------------------------------ serving 3D
 
-def measure_serving(nshots=48, max_active=8, load=0.8, budget_gb=150):
+def measure_serving(nshots=500, closed_shots=100, max_active=4, load=0.8, budget_gb=150):
     """The serving workload: a Poisson stream of 3D shots (cubes 128..384, 200..2000
-    steps) served by continuous batching and one at a time.  Open loop: arrivals
-    at `load` times the one-at-a-time service rate (calibrated here), reporting
-    p50/p99 latency.  Closed loop: every request queued at t = 0, reporting
-    shots/s.  Traces are compared bitwise between the modes."""
+    steps) served by continuous batching and one at a time.  Open loop: the whole
+    stream, arrivals at `load` times the one-at-a-time service rate (calibrated
+    here), reporting p50/p99 latency.  Closed loop: the first `closed_shots`
+    requests queued at t = 0, reporting shots/s.  Traces are compared bitwise
+    between the modes."""
     import torch
     from paper_2311_05038_b300 import fd, serving
     sizes = list(range(128, 385, 32))
@@ -346,7 +347,9 @@ def measure_serving(nshots=48, max_active=8, load=0.8, budget_gb=150):
     for i, (arr, n, nt) in enumerate(stream):
         vel = cache[(n, i % 2)]
         reqs.append(serving.Request(i, arr, wl.serving_3d_shot(i, n, nt, vel=vel.numpy()), vel))
-    out = {"workload": f"{nshots} 3D shots, cubes 128..384, 200..2000 steps, Poisson arrivals",
+    closed_shots = min(closed_shots, nshots)
+    out = {"workload": f"{nshots} 3D shots (open loop; closed loop: the first {closed_shots}), cubes 128..384, "
+                       f"200..2000 steps, Poisson arrivals at {load} x the one-at-a-time service rate",
            "rate_per_s": rate, "mean_service_s_one_at_a_time": mean_service, "budget_gb": budget_gb,
            "max_active": max_active}
     traces = {}
@@ -357,9 +360,10 @@ def measure_serving(nshots=48, max_active=8, load=0.8, budget_gb=150):
         res = srv.serve(reqs, realtime=True)
         open_loop = serving.summarize(res, time.perf_counter() - t0)
         t0 = time.perf_counter()
-        res_c = srv.serve(reqs, realtime=False)
+        res_c = srv.serve(reqs[:closed_shots], realtime=False)
         closed = serving.summarize(res_c, time.perf_counter() - t0)
-        out[mode] = {"open_loop": open_loop, "closed_loop": closed, "peak_hbm_gb": srv.pool.peak / 1e9}
+        out[mode] = {"policy": srv.policy, "open_loop": open_loop, "closed_loop": closed,
+                     "peak_hbm_gb": srv.pool.peak / 1e9}
         traces[mode] = [r.traces for r in res]
         srv.close()
     out["results_identical"] = all(np.array_equal(a, b) for a, b in zip(traces["continuous"],
@@ -635,8 +639,7 @@ def run_serving_line(args, rank):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if rank != 0:
         return
-    nshots = args.serve_shots if args.serve_shots != 48 else 500
-    r = measure_serving(nshots)
+    r = measure_serving(args.serve_shots)
     c = r["continuous"]
     line = {"metric": "shots/s (served 3D, continuous batching)", "value": c["closed_loop"]["shots_per_s"],
             "unit": "shots/s", "n_gpus": 1, "steps": 1, "warmup": 1,

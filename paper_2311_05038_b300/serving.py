@@ -15,12 +15,12 @@ so no request starves.
 
 Priorities.  Overlap alone shares the GPU evenly between the active shots,
 which stretches the longest shots and so the latency tail.  Each active shot's
-stream therefore carries a priority: the oldest active request the highest,
-the others ordered by their remaining work (shortest first), so the block
-scheduler gives the head of the queue the SMs it can use and fills the rest
-(tail waves, gaps between launches, small grids) with the others' blocks.  A
-shot changes priority by moving to another stream of its own
-(``fd_set_stream``, which keeps its work in order).
+stream therefore carries a priority, by default from an earliest-deadline
+ranking (a shot is due a fixed multiple of its stand-alone time after it
+arrives), so the block scheduler gives the most urgent shot the SMs it can use
+and fills the rest (tail waves, gaps between launches, small grids) with the
+others' blocks.  A shot changes priority by moving to another stream of its
+own (``fd_set_stream``, which keeps its work in order).
 
 Models are pooled per grid and reused for later requests of the same grid
 instead of being freed: ``cudaFree`` synchronises the whole device and would
@@ -165,22 +165,31 @@ class Server:
     chunk       time steps per fd_step call; depth: chunks queued per shot
     max_nt      largest step count a request may ask for (trace buffers are
                 sized for it once per pooled model)
-    priorities  give the oldest active shot the highest stream priority and the
-                others priorities by remaining work (default: on when more than
-                one shot may be active)
+    policy      how active shots are ranked onto stream priorities: "age"
+                (oldest first), "oldest+srpt" (the oldest, then shortest
+                remaining work), "deadline" (earliest arrival + slack x the
+                shot's work at ``rate_gupd``), or "none" (all at the default
+                priority).  Default "deadline" when more than one shot may be
+                active, else "none".
     max_bypass  how many later requests may be admitted ahead of a waiting
                 request that does not fit yet
     """
 
-    def __init__(self, max_active=8, budget_bytes=150 * 10**9, chunk=100, depth=2, max_nt=2000,
-                 priorities=None, max_bypass=8):
+    def __init__(self, max_active=4, budget_bytes=150 * 10**9, chunk=100, depth=2, max_nt=2000,
+                 policy=None, max_bypass=8, slack=2.0, rate_gupd=300.0):
         import torch
         self.torch = torch
         self.max_active = int(max_active)
         self.chunk = int(chunk)
         self.depth = int(depth)
         self.max_nt = int(max_nt)
-        self.priorities = self.max_active > 1 if priorities is None else bool(priorities)
+        if policy is None:
+            policy = "deadline" if self.max_active > 1 else "none"
+        if policy not in ("age", "oldest+srpt", "deadline", "none"):
+            raise ValueError(f"unknown policy {policy!r}")
+        self.policy = policy
+        self.slack = float(slack)
+        self.rate = float(rate_gupd) * 1e9
         self.max_bypass = int(max_bypass)
         self.greatest = None             # the device's highest stream priority, once known
         self.pool = ModelPool(budget_bytes, self._create, self._destroy)
@@ -241,15 +250,25 @@ class Server:
         fd.fd_set_trace_buffer(m.handle, None, shot.nt)
         return _Active(req, m, key, now, shot.nt)
 
+    def _rank(self, active):
+        """Active shots in priority order under the server's policy."""
+        if self.policy == "age":
+            return sorted(active, key=lambda a: (a.req.arrival, a.req.rid))
+        if self.policy == "oldest+srpt":
+            oldest = min(active, key=lambda a: (a.req.arrival, a.req.rid))
+            rest = sorted((a for a in active if a is not oldest), key=lambda a: (a.work_left(), a.req.rid))
+            return [oldest] + rest
+        # deadline: a shot is due slack times its stand-alone time after it arrived
+        return sorted(active, key=lambda a: (a.req.arrival + self.slack * a.req.shot.npoints * a.req.shot.nt
+                                             / self.rate, a.req.rid))
+
     def _reprioritise(self, active):
-        """Oldest request first, then shortest remaining work; priorities from the
-        device's greatest down to 0 (the default), the rest at 0."""
-        if not self.priorities or not active:
+        """Priorities from the device's greatest down to 0 (the default) in rank
+        order; the shots beyond the available levels stay at 0."""
+        if self.policy == "none" or not active:
             return
-        oldest = min(active, key=lambda a: (a.req.arrival, a.req.rid))
-        rest = sorted((a for a in active if a is not oldest), key=lambda a: (a.work_left(), a.req.rid))
         top = self.greatest if self.greatest is not None else 0
-        for i, a in enumerate([oldest] + rest):
+        for i, a in enumerate(self._rank(active)):
             self._set_priority(a.model, min(0, top + i))
 
     def serve(self, requests, realtime=True):
