@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--adjoint-shots", type=int, default=8, help="adjoint workload: shots per gradient")
+    ap.add_argument("--adjoint-lanes", type=int, default=4, help="adjoint workload: concurrent shot streams")
     ap.add_argument("--serve-shots", type=int, default=500, help="serving workload: requests in the stream")
     ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
@@ -375,10 +376,13 @@ def measure_serving(nshots=500, closed_shots=100, max_active=4, load=0.8, budget
 
 # ------------------------------------------------------------------------ adjoint 3D
 
-def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
+def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50, lanes=4):
     """Gradient of the trace misfit w.r.t. squared slowness for the adjoint
     workload (observed data from the +5 % anomaly model): time per gradient
-    over all shots, the forward share, and the device memory it held."""
+    over all shots, the forward share, and the device memory it held.  The
+    headline runs the shots on `lanes` concurrent streams (adjoint.ShotLanes);
+    the same gradient one shot at a time on one stream, and keeping every L'P^n
+    instead of checkpoints, are reported beside it."""
     import torch
     from paper_2311_05038_b300 import adjoint, fd
     shots, v_true = wl.adjoint_3d(n, nt, nshots)
@@ -391,34 +395,49 @@ def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
             m.run_shot(nt)
             observed.append(torch.from_numpy(m.traces(nt)).cuda())
     m0 = torch.from_numpy((1.0 / shots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
-    # untimed warm-up gradient on a small cut of the workload: loads the device code
-    # of every torch op on the path (casts, FP64 reduction, autograd) before timing
-    wshots, _ = wl.adjoint_3d(48, 40, 1)
-    wgeo = adjoint.Geometry.from_shot(wshots[0], checkpoint_every=10, sponge_vmax=vmax)
+    geos = [adjoint.Geometry.from_shot(s, checkpoint_every=checkpoint_every, sponge_vmax=vmax) for s in shots]
+    # untimed warm-up gradients on a small cut of the workload: load the device code
+    # of every op on both paths (casts, FP64 reduction, autograd) before timing
+    wshots, _ = wl.adjoint_3d(48, 40, 2)
+    wgeos = [adjoint.Geometry.from_shot(w, checkpoint_every=10, sponge_vmax=vmax) for w in wshots]
     wm = torch.from_numpy((1.0 / wshots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
-    adjoint.misfit_and_gradient(wm, wgeo, torch.zeros((40, len(wshots[0].receivers)), device="cuda"))
+    wobs = [torch.zeros((40, len(wshots[0].receivers)), device="cuda")] * 2
+    adjoint.misfit_and_gradient(wm, wgeos[0], wobs[0])
+    wl_lanes = adjoint.ShotLanes(wgeos, lanes=2)
+    wl_lanes.run(wm, wobs)
+    wl_lanes.close()
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
     base = torch.cuda.memory_allocated()
     t0 = time.perf_counter()
-    grad = torch.zeros_like(m0)
-    J = 0.0
-    for s, dobs in zip(shots, observed):
-        geo = adjoint.Geometry.from_shot(s, checkpoint_every=checkpoint_every, sponge_vmax=vmax)
-        Js, gs = adjoint.misfit_and_gradient(m0, geo, dobs)
-        J += Js
-        grad += gs
+    eng = adjoint.ShotLanes(geos, lanes=lanes)
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J, grad = eng.run(m0, observed)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    peak = torch.cuda.max_memory_allocated() - base
-    # forward-only time for the same shots, for the ratio
     t0 = time.perf_counter()
-    for s in shots:
-        geo = adjoint.Geometry.from_shot(s, checkpoint_every=checkpoint_every, sponge_vmax=vmax)
-        with torch.no_grad():
-            adjoint.Propagate.apply(m0, geo)
+    Jf, _ = eng.run(m0, observed, backward=False)
     torch.cuda.synchronize()
     fwd = time.perf_counter() - t0
+    peak = torch.cuda.max_memory_allocated() - base
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+    # one shot at a time on one stream (Propagate per shot)
+    t0 = time.perf_counter()
+    grad_1 = torch.zeros_like(m0)
+    for g, dobs in zip(geos, observed):
+        grad_1 += adjoint.misfit_and_gradient(m0, g, dobs)[1]
+    torch.cuda.synchronize()
+    el_1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for g in geos:
+        with torch.no_grad():
+            adjoint.Propagate.apply(m0, g)
+    torch.cuda.synchronize()
+    fwd_1 = time.perf_counter() - t0
+    rel_1 = float((grad_1 - grad).double().norm() / grad_1.double().norm())
     # the same gradient keeping every L'P^n instead of checkpoints (nt fields per shot)
     torch.cuda.empty_cache()
     torch.cuda.reset_peak_memory_stats()
@@ -431,15 +450,18 @@ def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50):
     torch.cuda.synchronize()
     el_s = time.perf_counter() - t0
     peak_s = torch.cuda.max_memory_allocated() - base
-    same = bool(torch.equal(grad, grad_s))
-    del grad_s
+    same = bool(torch.equal(grad_1, grad_s))
+    del grad_s, grad_1
     torch.cuda.empty_cache()
     return {"workload": f"{nshots} shots, {n}^3, {nt} steps, checkpoints every {checkpoint_every}",
-            "s_per_gradient": el, "forward_s": fwd, "gradient_over_forward": el / fwd, "misfit": J,
-            "peak_torch_memory_gb": peak / 1e9, "gupd_forward_equivalent": nshots * nt * n ** 3 / el / 1e9,
-            "grad_norm": float(grad.norm()),
-            "store_all": {"s_per_gradient": el_s, "gradient_over_forward": el_s / fwd,
-                          "peak_torch_memory_gb": peak_s / 1e9, "gradient_identical": same}}
+            "lanes": lanes, "s_per_gradient": el, "forward_s": fwd, "gradient_over_forward": el / fwd,
+            "misfit": J, "setup_s": setup, "peak_torch_memory_gb": peak / 1e9,
+            "gupd_forward": nshots * nt * n ** 3 / fwd / 1e9,
+            "gupd_forward_equivalent": nshots * nt * n ** 3 / el / 1e9, "grad_norm": float(grad.norm()),
+            "one_stream": {"s_per_gradient": el_1, "forward_s": fwd_1, "gupd_forward": nshots * nt * n ** 3 / fwd_1 / 1e9,
+                           "gradient_rel_l2_vs_lanes": rel_1},
+            "store_all": {"s_per_gradient": el_s, "gradient_over_forward": el_s / fwd_1,
+                          "peak_torch_memory_gb": peak_s / 1e9, "gradient_identical_to_one_stream": same}}
 
 
 # ------------------------------------------------------------------------ unfused 3D
@@ -586,7 +608,7 @@ def run_b300(args, dist, rank, local, world):
     adj = None
     if rank == 0 and not args.skip_adjoint:
         torch.cuda.empty_cache()
-        adj = measure_adjoint(nshots=args.adjoint_shots)
+        adj = measure_adjoint(nshots=args.adjoint_shots, lanes=args.adjoint_lanes)
     served = None
     if rank == 0 and not args.skip_serving:
         torch.cuda.empty_cache()

@@ -207,13 +207,28 @@ fd_status fd_get_damping_profile(fd_model *m, int axis, float *out, int cap);
  * segment; fd_step_lp_n and fd_adjoint_backward serve a run that keeps every
  * L'P^n instead of checkpoints. */
 
+/* v_dev[i] = 1 / sqrt(m_dev[i]) for n device floats of squared slowness m
+ * (s^2/m^2), in FP64 and rounded once to FP32; a non-positive m gives NaN, which
+ * model creation then rejects.  Asynchronous on stream (a cudaStream_t; NULL =
+ * the legacy default stream).  FD_EINVAL for NULL arrays or n = 0. */
+fd_status fd_velocity_from_slowness(const float *m_dev, float *v_dev, size_t n, void *stream);
+/* The gradient from accumulated images: grad_dev[i] = -(acc_0[i] + ... +
+ * acc_{nacc-1}[i]) / m_dev[i], where acc_dev holds nacc consecutive arrays of n
+ * floats (for instance one per group of shots run concurrently), each the sum
+ * over its shots and time steps of psi_{n+1} L'P^n, summed in array order.
+ * Asynchronous on stream.  FD_EINVAL for NULL arrays, nacc < 1 or n = 0. */
+fd_status fd_gradient_from_image(const float *acc_dev, int nacc, const float *m_dev, float *grad_dev, size_t n,
+                                 void *stream);
+
 /* Copy P (level n) and, if pold_dev is not NULL, Pold to dense device arrays
  * [nz][ny][nx] (asynchronous on the model's stream). */
 fd_status fd_get_wavefield_dev(fd_model *m, float *p_dev, float *pold_dev);
 /* Set P, Pold from dense device arrays and the step counter n (asynchronous). */
 fd_status fd_set_wavefield_dev(fd_model *m, const float *p_dev, const float *pold_dev, int n);
 /* Add values_dev[r] * w / (1 + a) to P at each receiver r (values: nrec floats on
- * the device; the adjoint-source injection). */
+ * the device; the adjoint-source injection).  Receivers that share a grid point
+ * have their values summed in receiver order first, so the result is the same
+ * from run to run (no atomics). */
 fd_status fd_inject_receivers(fd_model *m, const float *values_dev);
 /* grad_dev += P_adj * (L' p_dev) over dense [nz][ny][nx] device arrays, where
  * P_adj is the current level of the model adj and L' the stencil sum. */

@@ -91,7 +91,9 @@ def _make_function():
         def forward(ctx, m, geo):
             if not m.is_cuda:
                 raise ValueError("m must be a CUDA tensor")
-            v = torch.rsqrt(m.detach().to(torch.float32)).contiguous()
+            m32 = m.detach().to(torch.float32).contiguous()
+            v = torch.empty_like(m32)
+            fd.fd_velocity_from_slowness(m32, v, torch.cuda.current_stream())
             model = _model(torch, geo, v, with_source=True)
             nrec = len(geo.receivers)
             traces = torch.zeros((geo.nt, nrec), device=m.device, dtype=torch.float32)
@@ -147,8 +149,10 @@ def _make_function():
             model.close()
             ctx.model = None
             ctx.ckpts = None
-            grad_m = -(acc / m.detach().to(torch.float32)).to(m.dtype)
-            return grad_m, None
+            grad_m = torch.empty(geo.shape, device=m.device, dtype=torch.float32)
+            fd.fd_gradient_from_image(acc, m.detach().to(torch.float32).contiguous(), grad_m,
+                                      torch.cuda.current_stream())
+            return grad_m.to(m.dtype), None
 
     return _Propagate
 
@@ -162,3 +166,169 @@ def misfit_and_gradient(m, geo: Geometry, observed):
     J = 0.5 * (r.double() * r.double()).sum()
     J.backward()
     return float(J.detach()), mm.grad
+
+
+# ---------------------------------------------------------------- many shots at once
+
+class ShotLanes:
+    """The summed misfit J = 1/2 sum_shots |d_s(m) - observed_s|^2 and dJ/dm over
+    many shots of one grid, with the shots spread over ``lanes`` CUDA streams
+    that run at the same time.
+
+    A single shot of a mid-sized grid does not fill the B300 (at 256^3 a step
+    launch is under two waves of CTAs), so running shots side by side recovers
+    the idle SMs.  Each lane owns a forward and an adjoint model, its
+    checkpoint and segment buffers and a library stream, allocated once and
+    reused for every shot and every call; a host thread per lane issues its
+    shots' work (forward with checkpoints, residual, segment-wise adjoint), so a
+    lane never waits on another lane's launches.  Each lane accumulates its
+    shots' images psi_{n+1} L'P^n; ``fd_gradient_from_image`` sums the lanes and
+    divides by -m.  The per-shot arithmetic is that of ``Propagate``.
+
+    All shots must share the grid, h, dt, sponge and nt; sources, wavelets and
+    receivers may differ.
+    """
+
+    def __init__(self, geos, lanes=4):
+        import torch
+        self.torch = torch
+        self.geos = list(geos)
+        g0 = self.geos[0]
+        for g in self.geos:
+            if (g.ndim, tuple(g.shape), g.h, g.dt, g.nt, g.sponge_width, g.sponge_R, g.sponge_vmax,
+                    g.checkpoint_every) != (g0.ndim, tuple(g0.shape), g0.h, g0.dt, g0.nt, g0.sponge_width,
+                                           g0.sponge_R, g0.sponge_vmax, g0.checkpoint_every):
+                raise ValueError("all shots of a ShotLanes must share grid, time step, sponge and nt")
+        self.shape = tuple(g0.shape)
+        self.nt = g0.nt
+        self.K = max(1, int(g0.checkpoint_every))
+        self.nseg = (self.nt + self.K - 1) // self.K
+        nrec = max(len(g.receivers) for g in self.geos)
+        L = max(1, min(int(lanes), len(self.geos)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.acc = torch.zeros((L,) + self.shape, device=dev, dtype=torch.float32)
+        self.lanes = []
+        placeholder = 1e-3 * g0.h / g0.dt      # a velocity far inside the Courant limit
+        for _ in range(L):
+            handle, _ = fd.fd_stream_create(0)
+            ext = torch.cuda.ExternalStream(handle)
+            with torch.cuda.stream(ext):
+                v0 = torch.full(self.shape, placeholder, device=dev, dtype=torch.float32)
+                models = []
+                for _k in range(2):
+                    md = fd.Model(g0.ndim, self.shape, g0.h, g0.dt, v0, g0.sponge_width, g0.sponge_R, stream=handle)
+                    if g0.sponge_vmax is not None:
+                        fd.fd_set_sponge_vmax(md.handle, g0.sponge_vmax)
+                    models.append(md)
+                lane = {
+                    "stream": handle, "ext": ext, "fwd": models[0], "adj": models[1], "geo": None,
+                    "ckpts": torch.empty((self.nseg, 2) + self.shape, device=dev, dtype=torch.float32),
+                    "seg": torch.empty((self.K,) + self.shape, device=dev, dtype=torch.float32),
+                    "traces": torch.empty((self.nt, nrec), device=dev, dtype=torch.float32),
+                    "J": torch.zeros((), device=dev, dtype=torch.float64),
+                }
+            ext.synchronize()
+            self.lanes.append(lane)
+
+    def _shot(self, lane, geo, obs, backward, acc):
+        torch = self.torch
+        fwd, adj = lane["fwd"], lane["adj"]
+        if lane["geo"] is not geo:
+            fwd.set_source(geo.src, geo.wavelet)
+            fwd.set_receivers(geo.receivers)
+            adj.set_receivers(geo.receivers)
+            lane["geo"] = geo
+        nrec = len(geo.receivers)
+        traces = lane["traces"][:, :nrec] if nrec == lane["traces"].shape[1] else \
+            lane["traces"].view(-1)[:self.nt * nrec].view(self.nt, nrec)
+        fd.fd_reset(fwd.handle)
+        fd.fd_set_trace_buffer(fwd.handle, traces, self.nt)
+        ck = lane["ckpts"]
+        for s in range(self.nseg):
+            fd.fd_get_wavefield_dev(fwd.handle, ck[s, 0], ck[s, 1])
+            fd.fd_step(fwd.handle, min(self.K, self.nt - s * self.K))
+        r = (traces - obs).contiguous()
+        lane["J"] += (r.double() * r.double()).sum()
+        if not backward:
+            return
+        fd.fd_reset(adj.handle)
+        fd.fd_set_trace_buffer(fwd.handle, None, 0)       # the recompute records nothing
+        for s in range(self.nseg - 1, -1, -1):
+            n0 = s * self.K
+            n1 = min(n0 + self.K, self.nt)
+            fd.fd_set_wavefield_dev(fwd.handle, ck[s, 0], ck[s, 1], n0)
+            fd.fd_adjoint_segment(fwd.handle, adj.handle, n0, n1, lane["seg"], r, acc)
+
+    def _lane(self, li, v, observed, backward):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        lane = self.lanes[li]
+        with torch.cuda.stream(lane["ext"]):
+            fd.fd_set_velocity_dev(lane["fwd"].handle, v)
+            fd.fd_set_velocity_dev(lane["adj"].handle, v)
+            acc = self.acc[li]
+            acc.zero_()
+            lane["J"].zero_()
+            for j in range(li, len(self.geos), len(self.lanes)):
+                self._shot(lane, self.geos[j], observed[j], backward, acc)
+            fd.fd_synchronize(lane["fwd"].handle)
+            fd.fd_synchronize(lane["adj"].handle)
+
+    def run(self, m, observed, backward=True):
+        """(J, dJ/dm) for squared slowness m (FP32 CUDA tensor shaped like the grid)
+        and one observed trace array [nt][nrec] per shot; dJ/dm is None without
+        ``backward``."""
+        import concurrent.futures as cf
+        torch = self.torch
+        if len(observed) != len(self.geos):
+            raise ValueError("one observed trace array per shot")
+        m32 = m.detach().to(torch.float32).contiguous()
+        v = torch.empty_like(m32)
+        cur = torch.cuda.current_stream()
+        fd.fd_velocity_from_slowness(m32, v, cur)
+        obs = [o.detach().to(torch.float32).contiguous() for o in observed]
+        cur.synchronize()                       # v, m and the observed data are ready for every lane
+        with cf.ThreadPoolExecutor(len(self.lanes)) as ex:
+            for f in [ex.submit(self._lane, li, v, obs, backward) for li in range(len(self.lanes))]:
+                f.result()
+        J = 0.5 * float(sum(float(lane["J"]) for lane in self.lanes))
+        if not backward:
+            return J, None
+        grad = torch.empty_like(m32)
+        fd.fd_gradient_from_image(self.acc, m32, grad, cur)
+        return J, grad
+
+    def close(self):
+        for lane in self.lanes:
+            lane["fwd"].close()
+            lane["adj"].close()
+            fd.fd_stream_destroy(lane["stream"])
+        self.lanes = []
+
+
+class ShotsMisfit:
+    """torch.autograd.Function: squared slowness -> the summed misfit of a
+    ShotLanes' shots (an FP64 scalar), whose backward is their adjoint gradient."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, m, lanes: ShotLanes, observed):
+        if cls._fn is None:
+            import torch
+
+            class _ShotsMisfit(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, m, lanes, observed):
+                    J, grad = lanes.run(m, observed, backward=True)
+                    ctx.save_for_backward(grad)
+                    return torch.tensor(J, dtype=torch.float64, device=m.device)
+
+                @staticmethod
+                def backward(ctx, gJ):
+                    (grad,) = ctx.saved_tensors
+                    return (gJ.to(grad.dtype) * grad).to(grad.dtype), None, None
+
+            cls._fn = _ShotsMisfit
+        return cls._fn.apply(m, lanes, tuple(observed))

@@ -23,16 +23,18 @@
 
 namespace fdk {
 
-// values[r] * w / (1 + a) added to P at receiver r (pitched indices); atomically,
-// since two receivers may share a point.  With grad set, the injected value times
-// lp is added to grad as well (dense indices), completing grad += P * lp for the
-// level P had before the injection.
+// The receiver terms w g / (1 + a) added to P, one thread per receiver point:
+// the values of the receivers that share a point are summed first, in receiver
+// order, so no atomics are needed and the result does not depend on thread
+// timing.  With grad set, the injected value times lp is added to grad as well
+// (dense indices), completing grad += P * lp for the level P had before the
+// injection.
 __global__ void inject_kernel(float *P, const float *w, const float *ax, const float *ay, const float *az,
-                              const int64_t *idx, int nrec, const float *values, int nx, int ny, int px,
-                              int has_sponge, int ndim, const float *lp, float *grad)
+                              const int64_t *pt, const int *beg, const int *rec, int npt, const float *values,
+                              int nx, int ny, int px, int has_sponge, int ndim, const float *lp, float *grad)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
-        const int64_t i = idx[r];
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < npt; u += gridDim.x * blockDim.x) {
+        const int64_t i = pt[u];
         float a = 0.f;
         if (has_sponge) {
             const int64_t row = i / px;
@@ -41,13 +43,16 @@ __global__ void inject_kernel(float *P, const float *w, const float *ax, const f
             const int z = ndim == 3 ? (int)(row / ny) : (int)row;
             a = ax[x] + (ndim == 3 ? ay[y] : 0.f) + az[z];
         }
-        const float v = values[r] * w[i];
+        float g = values[rec[beg[u]]];
+        for (int j = beg[u] + 1; j < beg[u + 1]; ++j)
+            g += values[rec[j]];
+        const float v = g * w[i];
         const float add = a != 0.f ? __fdividef(v, 1.0f + a) : v;
-        atomicAdd(&P[i], add);
+        P[i] += add;
         if (grad) {
             const int64_t row = i / px;
             const int64_t d = row * nx + (i - row * px);
-            atomicAdd(&grad[d], add * lp[d]);
+            grad[d] = __fadd_rn(grad[d], __fmul_rn(add, lp[d]));
         }
     }
 }
@@ -119,6 +124,29 @@ __global__ void __launch_bounds__(256) imaging_product_kernel(const float *__res
     }
 }
 
+// v = m^(-1/2) for squared slowness m, in FP64 and rounded once to FP32 (a
+// non-positive or non-finite m gives NaN, which model creation rejects).
+__global__ void velocity_from_slowness_kernel(const float *__restrict__ m, float *__restrict__ v, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = (double)m[i];
+        v[i] = x > 0.0 ? (float)(1.0 / sqrt(x)) : __int_as_float(0x7fc00000);
+    }
+}
+
+// grad = -(acc_0 + ... + acc_{k-1}) / m: the images of k shot groups (consecutive
+// arrays of n floats) summed in that order, then divided by m.
+__global__ void gradient_from_image_kernel(const float *__restrict__ acc, int nacc, const float *__restrict__ m,
+                                           float *__restrict__ grad, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float s = acc[i];
+        for (int j = 1; j < nacc; ++j)
+            s += acc[(size_t)j * n + i];
+        grad[i] = -(s / m[i]);
+    }
+}
+
 }  // namespace fdk
 
 using namespace fdk;
@@ -171,10 +199,10 @@ static fd_status inject(fd_model *m, const float *values_dev, const float *lp_de
         if (st)
             return st;
     }
-    const int blocks = std::min((m->nrec + 255) / 256, 1184);
-    inject_kernel<<<blocks, 256, 0, m->stream>>>(m->buf[m->cur], m->w, m->ax, m->ay, m->az, m->d_rec, m->nrec,
-                                                 values_dev, m->nx, m->ny, m->px, m->has_sponge, m->d.ndim, lp_dev,
-                                                 grad_dev);
+    const int blocks = std::min((m->ninj + 255) / 256, 1184);
+    inject_kernel<<<blocks, 256, 0, m->stream>>>(m->buf[m->cur], m->w, m->ax, m->ay, m->az, m->d_inj_pt,
+                                                 m->d_inj_beg, m->d_inj_rec, m->ninj, values_dev, m->nx, m->ny,
+                                                 m->px, m->has_sponge, m->d.ndim, lp_dev, grad_dev);
     ++g_launches;
     FD_CUDA(cudaGetLastError(), "inject launch");
     return FD_OK;
@@ -271,4 +299,28 @@ extern "C" fd_status fd_adjoint_segment(fd_model *fwd, fd_model *adj, int n0, in
         if (fd_status st = fd_step_lp(fwd, lp_buf + (size_t)j * npts))
             return st;
     return fd_adjoint_backward(adj, n0, n1, lp_buf, g_dev, grad_dev);
+}
+
+extern "C" fd_status fd_velocity_from_slowness(const float *m_dev, float *v_dev, size_t n, void *stream)
+{
+    if (!m_dev || !v_dev || n == 0)
+        return fail(FD_EINVAL, "fd_velocity_from_slowness: bad arguments");
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+    velocity_from_slowness_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(m_dev, v_dev, n);
+    ++g_launches;
+    FD_CUDA(cudaGetLastError(), "slowness conversion launch");
+    return FD_OK;
+}
+
+extern "C" fd_status fd_gradient_from_image(const float *acc_dev, int nacc, const float *m_dev, float *grad_dev,
+                                            size_t n, void *stream)
+{
+    if (!acc_dev || nacc < 1 || !m_dev || !grad_dev || n == 0)
+        return fail(FD_EINVAL, "fd_gradient_from_image: bad arguments");
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+    gradient_from_image_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(acc_dev, nacc, m_dev,
+                                                                                       grad_dev, n);
+    ++g_launches;
+    FD_CUDA(cudaGetLastError(), "gradient launch");
+    return FD_OK;
 }

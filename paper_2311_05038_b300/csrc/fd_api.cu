@@ -203,6 +203,9 @@ static void free_model(fd_model *m)
     cudaFree(m->d_err);
     cudaFree(m->d_stats);
     cudaFree(m->d_rec);
+    cudaFree(m->d_inj_pt);
+    cudaFree(m->d_inj_beg);
+    cudaFree(m->d_inj_rec);
     cudaFree(m->d_amp);
     cudaFree(m->stage);
     for (float *d : m->deriv)
@@ -498,19 +501,64 @@ extern "C" fd_status fd_set_receivers(fd_model *m, const int *xyz_host, int nrec
         pit[r] = ((int64_t)iz * m->ny + iy) * m->px + ix;
         dense[r] = ((int64_t)iz * m->ny + iy) * m->nx + ix;
     }
+    // receivers grouped by grid point (points ascending, receivers ascending within one)
+    std::vector<int> order(nrec);
+    for (int r = 0; r < nrec; ++r)
+        order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pit[a] < pit[b]; });
+    std::vector<int64_t> upt;
+    std::vector<int> ubeg;
+    for (int j = 0; j < nrec; ++j) {
+        if (j == 0 || pit[order[j]] != pit[order[j - 1]]) {
+            upt.push_back(pit[order[j]]);
+            ubeg.push_back(j);
+        }
+    }
+    ubeg.push_back(nrec);
     if (nrec > m->rec_cap) {
-        int64_t *p = nullptr;
-        FD_CUDA(cudaMalloc((void **)&p, (size_t)nrec * sizeof(int64_t)), "receiver allocation");
+        int64_t *p = nullptr, *q = nullptr;
+        int *b = nullptr, *o = nullptr;
+        cudaError_t e = cudaMalloc((void **)&p, (size_t)nrec * sizeof(int64_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&q, (size_t)nrec * sizeof(int64_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&b, (size_t)(nrec + 1) * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&o, (size_t)nrec * sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            cudaFree(q);
+            cudaFree(b);
+            cudaFree(o);
+            return cuda_fail(e, "receiver allocation");
+        }
         cudaStreamSynchronize(m->stream);
         cudaFree(m->d_rec);
+        cudaFree(m->d_inj_pt);
+        cudaFree(m->d_inj_beg);
+        cudaFree(m->d_inj_rec);
         m->d_rec = p;
+        m->d_inj_pt = q;
+        m->d_inj_beg = b;
+        m->d_inj_rec = o;
         m->rec_cap = nrec;
     }
-    if (nrec > 0)
+    if (nrec > 0) {
         FD_CUDA(cudaMemcpyAsync(m->d_rec, pit.data(), (size_t)nrec * sizeof(int64_t), cudaMemcpyHostToDevice,
                                 m->stream),
                 "receiver upload");
+        FD_CUDA(cudaMemcpyAsync(m->d_inj_pt, upt.data(), upt.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                m->stream),
+                "receiver upload");
+        FD_CUDA(cudaMemcpyAsync(m->d_inj_beg, ubeg.data(), ubeg.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                m->stream),
+                "receiver upload");
+        FD_CUDA(cudaMemcpyAsync(m->d_inj_rec, order.data(), (size_t)nrec * sizeof(int), cudaMemcpyHostToDevice,
+                                m->stream),
+                "receiver upload");
+    }
     FD_CUDA(cudaStreamSynchronize(m->stream), "receiver upload");
+    m->ninj = (int)upt.size();
     if (nrec != m->nrec) {
         // the trace layout changed: a caller buffer no longer fits, an owned one is re-laid out
         if (!m->traces_owned)

@@ -48,6 +48,12 @@ struct fd_model {
     int nrec = 0;
     int64_t *d_rec = nullptr;  // pitched indices (device)
     int rec_cap = 0;
+    // receivers grouped by grid point, for a deterministic injection (no atomics):
+    // point u is d_inj_pt[u] (pitched), its receivers d_inj_rec[d_inj_beg[u] .. d_inj_beg[u+1])
+    int64_t *d_inj_pt = nullptr;
+    int *d_inj_beg = nullptr;
+    int *d_inj_rec = nullptr;
+    int ninj = 0;
     std::vector<int64_t> rec_dense;
 
     float *traces = nullptr;

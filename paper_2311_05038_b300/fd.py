@@ -43,7 +43,8 @@ EXPORTS = [
     "fd_set_sponge_vmax", "fd_batch_set_fault", "fd_step_lp", "fd_imaging_product",
     "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
     "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward", "fd_debug_stall_stage",
-    "fd_set_stream", "fd_stream_create", "fd_stream_destroy",
+    "fd_set_stream", "fd_stream_create", "fd_stream_destroy", "fd_velocity_from_slowness",
+    "fd_gradient_from_image",
 ]
 
 
@@ -127,6 +128,8 @@ _SIGS = {
     "fd_set_stream": (_i, [_vp, _vp]),
     "fd_stream_create": (_i, [_i, ctypes.POINTER(_vp), _ip]),
     "fd_stream_destroy": (_i, [_vp]),
+    "fd_velocity_from_slowness": (_i, [_vp, _vp, _sz, _vp]),
+    "fd_gradient_from_image": (_i, [_vp, _i, _vp, _vp, _sz, _vp]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -436,6 +439,23 @@ def fd_inject_receivers_image(m: int, values_dev, lp_dev, grad_dev):
     """fd_inject_receivers, also adding each injected value times lp_dev to grad_dev."""
     _check(_lib.fd_inject_receivers_image(m, None if values_dev is None else _dev_ptr(values_dev),
                                           _dev_ptr(lp_dev), _dev_ptr(grad_dev)), "fd_inject_receivers_image")
+
+
+def fd_velocity_from_slowness(m_dev, v_dev, stream=None):
+    """v = m^(-1/2) elementwise (device tensors of equal size)."""
+    if m_dev.numel() != v_dev.numel():
+        raise ValueError("m and v differ in size")
+    _check(_lib.fd_velocity_from_slowness(_dev_ptr(m_dev), _dev_ptr(v_dev), m_dev.numel(), _stream_ptr(stream)),
+           "fd_velocity_from_slowness")
+
+
+def fd_gradient_from_image(acc_dev, m_dev, grad_dev, stream=None):
+    """grad = -(sum over the leading axis of acc) / m; acc shaped (k,) + m.shape or m.shape."""
+    n = m_dev.numel()
+    if acc_dev.numel() % n or grad_dev.numel() != n:
+        raise ValueError("acc, m and grad sizes do not match")
+    _check(_lib.fd_gradient_from_image(_dev_ptr(acc_dev), acc_dev.numel() // n, _dev_ptr(m_dev), _dev_ptr(grad_dev),
+                                       n, _stream_ptr(stream)), "fd_gradient_from_image")
 
 
 def fd_step_lp_n(m: int, nsteps: int, lp_buf):

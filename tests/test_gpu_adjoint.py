@@ -43,13 +43,18 @@ def observed(fd, shot, vt, vmax):
         return torch.from_numpy(m.traces(shot.nt)).cuda()
 
 
+def velocity_of(m):
+    """The FP32 velocity the library derives from squared slowness m (FP64, one rounding)."""
+    return (1.0 / np.sqrt(m.cpu().numpy().astype(np.float64))).astype(np.float32)
+
+
 def gpu_and_oracle(fd, oracle, shot, observed_np, vmax=3200.0, K=25):
     import torch
     from paper_2311_05038_b300 import adjoint
     geo = adjoint.Geometry.from_shot(shot, checkpoint_every=K, sponge_vmax=vmax)
     m = torch.from_numpy((1.0 / shot.vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
     J, g = adjoint.misfit_and_gradient(m, geo, torch.from_numpy(observed_np.astype(np.float32)).cuda())
-    Jr, gr, _ = oracle.misfit_gradient(shot.ndim, shot.shape, shot.h, shot.dt, torch.rsqrt(m).cpu().numpy(),
+    Jr, gr, _ = oracle.misfit_gradient(shot.ndim, shot.shape, shot.h, shot.dt, velocity_of(m),
                                        sponge_width=shot.sponge_width, src=shot.src, wavelet=shot.wavelet,
                                        receivers=shot.receivers, nsteps=shot.nt, observed=observed_np,
                                        sponge_vmax=vmax)
@@ -76,8 +81,23 @@ def test_gradient_matches_oracle_for_a_misfit(fdlib, oracle, ndim, tol):
     shot, vt = case(ndim)
     dobs = observed(fdlib, shot, vt, 3200.0).cpu().numpy().astype(np.float64)
     J, g, Jr, gr = gpu_and_oracle(fdlib, oracle, shot, dobs)
+    print(f"{ndim}D reflection misfit: J {J:.6e} vs {Jr:.6e}, gradient rel L2 {pl.rel_l2(g, gr):.2e}")
     assert J == pytest.approx(Jr, rel=1e-3)
     assert pl.rel_l2(g, gr) <= tol
+
+
+def test_gradient_matches_oracle_in_transmission_2d(fdlib, oracle):
+    """The 2D case with the receivers below the anomaly (transmission): the
+    residual is then a large part of the traces, FP32 rounding is not amplified,
+    and the gradient matches the FP64 one to 1e-4."""
+    shot, vt = case(2)
+    shot.receivers = np.array([(x, 0, 50) for x in range(6, 66, 3)], np.int32)
+    dobs = observed(fdlib, shot, vt, 3200.0).cpu().numpy().astype(np.float64)
+    J, g, Jr, gr = gpu_and_oracle(fdlib, oracle, shot, dobs)
+    err = pl.rel_l2(g, gr)
+    print(f"2D transmission misfit: J {J:.6e} vs {Jr:.6e}, gradient rel L2 {err:.2e}")
+    assert J == pytest.approx(Jr, rel=1e-4)
+    assert err <= 1e-4
 
 
 def test_gradient_matches_finite_differences(fdlib):
@@ -251,6 +271,7 @@ def test_gradient_full_size_finite_differences(fdlib):
         _, g = adjoint.misfit_and_gradient(m, geo, dobs)
         an = float((g.double() * dm.double()).sum())
         fdv = (misfit(m + eps * dm, dobs) - misfit(m - eps * dm, dobs)) / (2 * eps)
+        print(f"256^3 finite differences, {what}: relative difference {abs(fdv - an) / abs(an):.2e}")
         assert abs(fdv - an) <= tol * abs(an), (what, fdv, an)
 
     zero = torch.zeros((s.nt, len(s.receivers)), device="cuda")
@@ -346,3 +367,133 @@ def test_store_all_entry_points_check_arguments(fdlib):
         assert e.value.status == -1
         fdlib.fd_adjoint_backward(adj.handle, 0, 3, lp, g, grad)
         assert fdlib.fd_get_step(adj.handle) == 3
+
+
+def test_slowness_and_gradient_conversions_are_exact(fdlib):
+    """fd_velocity_from_slowness rounds m^(-1/2) once from FP64; fd_gradient_from_image
+    sums the images in array order and divides by -m in FP32: both bitwise equal to
+    the same operations in NumPy."""
+    import torch
+    rng = np.random.default_rng(40)
+    n = 100_003
+    m = (1.0 / rng.uniform(1500, 4500, n) ** 2).astype(np.float32)
+    v = torch.empty(n, device="cuda")
+    fdlib.fd_velocity_from_slowness(torch.from_numpy(m).cuda(), v)
+    np.testing.assert_array_equal(v.cpu().numpy(), (1.0 / np.sqrt(m.astype(np.float64))).astype(np.float32))
+    acc = rng.standard_normal((3, n)).astype(np.float32)
+    grad = torch.empty(n, device="cuda")
+    fdlib.fd_gradient_from_image(torch.from_numpy(acc).cuda(), torch.from_numpy(m).cuda(), grad)
+    s = (acc[0] + acc[1]) + acc[2]
+    np.testing.assert_array_equal(grad.cpu().numpy(), -(s / m))
+    t = torch.ones(3, device="cuda")
+    assert fdlib._lib.fd_gradient_from_image(t.data_ptr(), 0, t.data_ptr(), t.data_ptr(), 3, None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_velocity_from_slowness(t.data_ptr(), None, 3, None) == fdlib.FD_EINVAL
+
+
+def test_coincident_receivers_inject_deterministically(fdlib, oracle):
+    """Receivers that share a point: their values are summed before the injection,
+    so repeated runs agree bitwise and match the oracle's sum at that point."""
+    import torch
+    shape = (21, 17, 29)
+    shot = _random_shot(shape, seed=41)
+    shot.receivers = np.array([(5, 6, 7), (5, 6, 7), (9, 2, 3), (5, 6, 7), (9, 2, 3)], np.int32)
+    vals = torch.tensor([1.0, -2.5, 0.75, 4.0, 3.0], device="cuda")
+    out = []
+    for _ in range(2):
+        with fdlib.Model.from_shot(shot) as m:
+            fdlib.fd_set_wavefield(m.handle, np.zeros(shape, np.float32), np.zeros(shape, np.float32), 0)
+            lp = torch.ones(shape, device="cuda")
+            grad = torch.zeros(shape, device="cuda")
+            fdlib.fd_inject_receivers_image(m.handle, vals, lp, grad)
+            torch.cuda.synchronize()
+            out.append((m.wavefield(), grad.cpu().numpy()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    w = (shot.dt * shot.vel.astype(np.float64) / shot.h) ** 2
+    emax = oracle.sponge_eta_max(float(shot.vel.max()), 3, shot.h, 1e-3)
+    for (x, y, z), g in (((5, 6, 7), 1.0 - 2.5 + 4.0), ((9, 2, 3), 0.75 + 3.0)):
+        a = shot.dt * (oracle.sponge_profile(shape[2], 3, emax)[x] + oracle.sponge_profile(shape[1], 3, emax)[y]
+                       + oracle.sponge_profile(shape[0], 3, emax)[z])
+        want = g * w[z, y, x] / (1 + a)
+        assert out[0][0][z, y, x] == pytest.approx(want, rel=1e-6)
+        assert out[0][1][z, y, x] == pytest.approx(want, rel=1e-6)
+
+
+def _lanes_case(n=36, nt=140, nshots=3):
+    shots, v_true = wl.adjoint_3d(n, nt, nshots)
+    return shots, v_true, 4000.0 * 1.05
+
+
+def test_shot_lanes_match_the_per_shot_gradients(fdlib):
+    """ShotLanes (shots on concurrent streams, one image per lane) gives the summed
+    misfit and gradient of per-shot Propagate calls, and ShotsMisfit carries it
+    through autograd."""
+    import torch
+    from paper_2311_05038_b300 import adjoint
+    shots, v_true, vmax = _lanes_case()
+    geos = [adjoint.Geometry.from_shot(s, checkpoint_every=30, sponge_vmax=vmax) for s in shots]
+    m = torch.from_numpy((1.0 / shots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    obs = []
+    for s in shots:
+        st = wl.Shot(3, s.shape, s.h, s.dt, s.nt, v_true, s.src, s.wavelet, s.receivers, sponge_width=s.sponge_width)
+        with fdlib.Model.from_shot(st) as mt:
+            fdlib.fd_set_sponge_vmax(mt.handle, vmax)
+            mt.run_shot(s.nt)
+            obs.append(torch.from_numpy(mt.traces(s.nt)).cuda())
+    J_ref, g_ref = 0.0, torch.zeros_like(m)
+    for geo, o in zip(geos, obs):
+        J, g = adjoint.misfit_and_gradient(m, geo, o)
+        J_ref += J
+        g_ref += g
+    lanes = adjoint.ShotLanes(geos, lanes=2)
+    try:
+        for _ in range(2):                       # buffers and models are reused across calls
+            J, g = lanes.run(m, obs)
+            assert J == pytest.approx(J_ref, rel=1e-6)
+            assert pl.rel_l2(g.cpu().numpy(), g_ref.cpu().numpy()) <= 1e-6
+        mm = m.clone().requires_grad_(True)
+        Jt = adjoint.ShotsMisfit.apply(mm, lanes, obs)
+        Jt.backward()
+        assert float(Jt) == pytest.approx(J_ref, rel=1e-6)
+        np.testing.assert_array_equal(mm.grad.cpu().numpy(), g.cpu().numpy())
+        Jf, none = lanes.run(m, obs, backward=False)
+        assert none is None and Jf == pytest.approx(J_ref, rel=1e-6)
+    finally:
+        lanes.close()
+
+
+@pytest.mark.parametrize("data", ["zero", "anomaly"])
+def test_gradient_matches_oracle_on_adjoint_workload_64(fdlib, oracle, data):
+    """The adjoint workload cut down to 64^3 (its GRF model, sponge 20, +5 % anomaly
+    data), 2 shots of 400 steps through ShotLanes, against the FP64 discrete
+    adjoint of the oracle summed over the shots."""
+    import torch
+    from paper_2311_05038_b300 import adjoint
+    shots, v_true = wl.adjoint_3d(64, 400, 2)
+    vmax = 4000.0 * 1.05
+    geos = [adjoint.Geometry.from_shot(s, checkpoint_every=50, sponge_vmax=vmax) for s in shots]
+    m = torch.from_numpy((1.0 / shots[0].vel.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    obs = []
+    for s in shots:
+        if data == "zero":
+            obs.append(np.zeros((s.nt, len(s.receivers))))
+            continue
+        _, _, tr = oracle.run(3, s.shape, s.h, s.dt, v_true, sponge_width=s.sponge_width, src=s.src,
+                              wavelet=s.wavelet, receivers=s.receivers, nsteps=s.nt, sponge_vmax=vmax)
+        obs.append(tr)
+    lanes = adjoint.ShotLanes(geos, lanes=2)
+    try:
+        J, g = lanes.run(m, [torch.from_numpy(o.astype(np.float32)).cuda() for o in obs])
+    finally:
+        lanes.close()
+    Jr, gr = 0.0, 0.0
+    for s, o in zip(shots, obs):
+        Js, gs, _ = oracle.misfit_gradient(3, s.shape, s.h, s.dt, velocity_of(m), sponge_width=s.sponge_width,
+                                           src=s.src, wavelet=s.wavelet, receivers=s.receivers, nsteps=s.nt,
+                                           observed=o.astype(np.float32).astype(np.float64), sponge_vmax=vmax)
+        Jr += Js
+        gr = gr + gs
+    err = pl.rel_l2(g.cpu().numpy(), gr)
+    print(f"64^3 adjoint workload, {data} data: misfit {J:.6e} vs {Jr:.6e}, gradient rel L2 {err:.2e}")
+    assert J == pytest.approx(Jr, rel=1e-4)
+    assert err <= 1e-4
