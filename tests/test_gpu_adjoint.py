@@ -247,7 +247,8 @@ def test_gradient_full_size_finite_differences(fdlib):
     - Zero observed data, J = 1/2 |d|^2, along three smooth random directions of
       2 % rms: agreement within 1e-3 (measured 1e-4 .. 3e-4 at eps = 0.01).
     - The real misfit against data of the +5 % anomaly model, along the anomaly's
-      own Gaussian blob, where J is close to quadratic: within 1e-2.
+      own Gaussian blob, where J is close to quadratic: within 1e-3 (measured
+      1.3e-4 at eps = 0.05).
 
     The real misfit is not differenced along smooth global directions: the
     receivers sit three cells from the source, so such a direction changes the
@@ -286,7 +287,7 @@ def test_gradient_full_size_finite_differences(fdlib):
         mt.run_shot(s.nt)
         dobs = torch.from_numpy(mt.traces(s.nt)).cuda()
     blob = torch.from_numpy((v_true.astype(np.float64) / s.vel - 1.0).astype(np.float32)).cuda()
-    check(dobs, -2.0 * blob * m, 0.05, 1e-2, "anomaly data, blob direction")
+    check(dobs, -2.0 * blob * m, 0.05, 1e-3, "anomaly data, blob direction")
 
 
 @pytest.mark.parametrize("shape", [(21, 17, 29), (33, 45), (20, 16, 32)])
