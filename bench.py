@@ -258,8 +258,9 @@ def run_reference(args, dist, rank, world):
 # ------------------------------------------------------------------------ batched 2D
 
 def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
-    """The batched 2D workload served two ways on this GPU: one shot at a time
-    (fd_run_shot per shot, back to back) and all shots in one persistent batch
+    """The batched 2D workload served three ways on this GPU: one shot at a time
+    (fd_run_shot per shot, back to back on one stream), one shot at a time on
+    each of 8 streams at once, and all shots in one persistent batch
     (autotuned).  Returns a summary dict; results are compared bitwise."""
     import torch
     from paper_2311_05038_b300 import fd
@@ -288,6 +289,24 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
     plain_launches = (fd.fd_kernel_launch_count() - launches0) // (repeats + 1)
     ref = [m.traces(nt).copy() for m in models]
     ref_p = [m.wavefield() for m in models[:8]]
+    # one shot at a time per stream, on `nstreams` streams at once (fd_run_shot per
+    # shot; shot i on stream i mod nstreams)
+    nstreams = 8
+    handles = [fd.fd_stream_create(0)[0] for _ in range(nstreams)]
+    smodels = [fd.Model.from_shot(s, stream=handles[i % nstreams]) for i, s in enumerate(shots)]
+
+    def streams():
+        for m in smodels:
+            m.run_shot(nt)
+        for m in smodels:
+            fd.fd_synchronize(m.handle)
+
+    t_streams = timed(streams)
+    same_streams = all(np.array_equal(m.traces(nt), r) for m, r in zip(smodels, ref))
+    for m in smodels:
+        m.close()
+    for h in handles:
+        fd.fd_stream_destroy(h)
     batch = fd.Batch(models)
     if tile >= 0:
         batch.set_tuning(tile=tile, steps_per_launch=nt, ctas_per_sm=0, group_mb=group_mb)
@@ -307,9 +326,12 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
         "updates": updates,
         "plain": {"s": t_plain, "shots_per_s": nshots / t_plain, "gupd": updates / t_plain / 1e9,
                   "launches": int(plain_launches)},
+        "plain_streams": {"streams": nstreams, "s": t_streams, "shots_per_s": nshots / t_streams,
+                          "gupd": updates / t_streams / 1e9, "results_identical": bool(same_streams)},
         "batched": {"s": t_batch, "shots_per_s": nshots / t_batch, "gupd": updates / t_batch / 1e9,
                     "launches": int(batch_launches), "tuning": tuning},
         "speedup": t_plain / t_batch,
+        "speedup_vs_streams": t_streams / t_batch,
         "results_identical": bool(same),
     }
 
