@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-unfused", action="store_true")
+    ap.add_argument("--skip-fused", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--adjoint-shots", type=int, default=8, help="adjoint workload: shots per gradient")
@@ -486,6 +487,40 @@ def measure_adjoint(n=256, nt=1500, nshots=8, checkpoint_every=50, lanes=4):
                           "peak_torch_memory_gb": peak_s / 1e9, "gradient_identical_to_one_stream": same}}
 
 
+# ------------------------------------------------------------------------ fused pairs 3D
+
+def measure_time_fusion(shot, model, stream, traces, shots=3):
+    """The benchmark shot with two time steps per launch (fd_set_time_fusion): Gupd/s
+    over `shots` whole shots (one warm-up shot first), 10 algorithmic bytes per
+    update, and the traces compared bitwise with the single-step run's."""
+    import torch
+    from paper_2311_05038_b300 import fd
+    ref = traces.clone()
+    m2 = fd.Model.from_shot(shot, stream=stream)
+    m2.set_time_fusion(2)
+    m2.run_shot(shot.nt, traces)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(traces, ref))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = fd.fd_kernel_launch_count()
+    e0.record(stream)
+    for _ in range(shots):
+        m2.run_shot(shot.nt, traces)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = fd.fd_kernel_launch_count() - l0
+    t = e0.elapsed_time(e1) / 1e3
+    m2.close()
+    peak, _ = measured_hbm_peak()
+    npts = shot.npoints
+    pair_s = t / (shots * shot.nt / 2)
+    return {"gupd": shots * shot.nt * npts / t / 1e9, "ms_per_shot": t / shots * 1e3,
+            "avg_pair_launch_us": pair_s * 1e6, "launches_per_shot": launches / shots,
+            "bytes_per_update": 10, "achieved_GBs": 20 * npts / pair_s / 1e9,
+            "frac_algorithmic": 20 * npts / pair_s / 1e9 / peak, "traces_identical_to_single_steps": same}
+
+
 # ------------------------------------------------------------------------ unfused 3D
 
 def measure_unfused(shot, model, stream, reps=20):
@@ -569,6 +604,10 @@ def run_b300(args, dist, rank, local, world):
     avg_launch_s = ev0.elapsed_time(ev1) / 1e3 / step_launches
     achieved = BYTES_PER_UPDATE * npts / avg_launch_s / 1e9
     peak, peak_kind = measured_hbm_peak()
+
+    fused = None
+    if rank == 0 and not args.skip_fused:
+        fused = measure_time_fusion(shot, model, stream, traces, args.steps)
 
     unfused = None
     if rank == 0 and not args.skip_unfused:
@@ -660,6 +699,7 @@ def run_b300(args, dist, rank, local, world):
             "serving_3d": served,
             "adjoint_3d": adj,
             "unfused_3d": unfused,
+            "time_fusion_3d": fused,
         }
         print(json.dumps(line), flush=True)
 

@@ -158,6 +158,19 @@ fd_status fd_set_wavefield(fd_model *m, const float *p_host, const float *pold_h
 /* Advance nsteps >= 0 time steps, asynchronously on the model's stream. */
 fd_status fd_step(fd_model *m, int nsteps);
 
+/* Time steps per launch for later fd_step / fd_run_shot calls: 1 (the default)
+ * or, for 3D models, 2.  With 2, one launch advances two steps (temporal fusion:
+ * the first step is evaluated on each CTA's column widened by the stencil
+ * radius, so the second has its neighbours without leaving the chip), reading
+ * P^{n-1}, P^n and w once and writing P^{n+1} and P^{n+2}: 20 bytes per point
+ * for two updates instead of 32.  The levels and traces are bitwise those of
+ * single steps; an odd step count ends with one single step.  The first call
+ * with 2 allocates two more wavefield buffers (2 x 4 nx*ny*nz bytes, padded
+ * rows) kept until the model is destroyed.  The L'P and imaging steps of the
+ * adjoint and the fd_debug_stall_stage hook always run single steps.  Errors:
+ * FD_EINVAL (steps not 1 or 2, or 2 for a 2D model), FD_ECUDA / FD_ENOMEM. */
+fd_status fd_set_time_fusion(fd_model *m, int steps);
+
 /* One shot: reset, record into traces_dev ([nt][nrec] device buffer, or NULL
  * for a library-owned buffer), advance nt steps.  Asynchronous. */
 fd_status fd_run_shot(fd_model *m, int nt, float *traces_dev);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libfd.so")
-SOURCES = ["fd_api.cu", "fd_kernels.cu", "fd_batch.cu", "fd_unfused.cu", "fd_adjoint.cu"]
+SOURCES = ["fd_api.cu", "fd_kernels.cu", "fd_t2.cu", "fd_batch.cu", "fd_unfused.cu", "fd_adjoint.cu"]
 HEADERS = ["fd_internal.h", "fd_model.h", "fd_trace.h", "ptx.cuh", "stencil.cuh"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

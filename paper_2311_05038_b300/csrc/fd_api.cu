@@ -210,6 +210,8 @@ static void free_model(fd_model *m)
     cudaFree(m->stage);
     for (float *d : m->deriv)
         cudaFree(d);
+    cudaFree(m->xbuf[0]);
+    cudaFree(m->xbuf[1]);
     if (m->traces_owned)
         cudaFree(m->traces);
     if (m->handoff)
@@ -646,12 +648,92 @@ static fd_status flush_pending(fd_model *m)
     return FD_OK;
 }
 
+// Two fused steps: levels n+1, n+2 into the spare buffers, which then take the
+// places of buf[] (with their maps).  The launch gathers the receiver rows still
+// owed for its two input levels (pending_old from Pold, m->pending_row from P).
+static fd_status step_pair(fd_model *m, int &pending_old)
+{
+    T2Params p{};
+    float w4[4];
+    fd_stencil_weights(w4);
+    p.c1 = w4[0];
+    p.c2 = w4[1];
+    p.c3 = w4[2];
+    p.c4 = w4[3];
+    const int c = m->cur;
+    p.P1 = m->buf[c];
+    p.P0 = m->buf[c ^ 1];
+    p.out2 = m->xbuf[0];
+    p.out3 = m->xbuf[1];
+    p.ax = m->ax;
+    p.ay = m->ay;
+    p.az = m->az;
+    p.nx = m->nx;
+    p.ny = m->ny;
+    p.nz = m->nz;
+    p.px = m->px;
+    p.bz = m->t2_bz;
+    p.has_sponge = m->has_sponge;
+    p.sx = m->sx;
+    p.sy = m->sy;
+    p.sz = m->sz;
+    const int na = (int)m->amp.size();
+    p.src_on0 = m->src_on && m->n < na;
+    p.amp0 = p.src_on0 ? m->amp[m->n] : 0.f;
+    p.src_on1 = m->src_on && m->n + 1 < na;
+    p.amp1 = p.src_on1 ? m->amp[m->n + 1] : 0.f;
+    p.rec_idx = m->d_rec;
+    p.nrec = m->nrec;
+    p.trace_prev0 = pending_old >= 0 ? m->traces + (size_t)pending_old * m->nrec : nullptr;
+    p.trace_prev1 = m->pending_row >= 0 ? m->traces + (size_t)m->pending_row * m->nrec : nullptr;
+    p.err = m->d_err;
+    cudaError_t e = launch_step3d_t2(m->t2p1_map[c], m->t2e_map[c ^ 1], m->t2w_map, p, m->t2_nchunks, m->stream);
+    ++g_launches;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "fused step kernel launch");
+    // level n+1 (in xbuf[0]) becomes Pold, level n+2 (in xbuf[1]) becomes P
+    std::swap(m->buf[c ^ 1], m->xbuf[0]);
+    std::swap(m->halo_map[c ^ 1], m->xhalo_map[0]);
+    std::swap(m->tile_map[c ^ 1], m->xtile_map[0]);
+    std::swap(m->t2p1_map[c ^ 1], m->xt2p1_map[0]);
+    std::swap(m->t2e_map[c ^ 1], m->xt2e_map[0]);
+    std::swap(m->buf[c], m->xbuf[1]);
+    std::swap(m->halo_map[c], m->xhalo_map[1]);
+    std::swap(m->tile_map[c], m->xtile_map[1]);
+    std::swap(m->t2p1_map[c], m->xt2p1_map[1]);
+    std::swap(m->t2e_map[c], m->xt2e_map[1]);
+    const bool rec = m->nrec > 0 && m->traces;
+    pending_old = rec && m->n < m->trace_rows ? m->n : -1;
+    m->pending_row = rec && m->n + 1 < m->trace_rows ? m->n + 1 : -1;
+    m->n += 2;
+    return FD_OK;
+}
+
 // nsteps time steps; if lp is set (nsteps == 1), the step also writes L'P of the
 // level it consumes to lp; if img_grad is set (nsteps == 1), it adds Pn * img_lp
 // to img_grad (all dense [nz][ny][nx]).
 static fd_status step_n(fd_model *m, int nsteps, float *lp, const float *img_lp = nullptr,
                         float *img_grad = nullptr)
 {
+    int pending_old = -1;   // a receiver row of the Pold level still owed (after a fused pair)
+    auto flush_old = [&]() -> fd_status {
+        if (pending_old < 0)
+            return FD_OK;
+        cudaError_t e = launch_gather(m->buf[m->cur ^ 1], m->d_rec, m->nrec,
+                                      m->traces + (size_t)pending_old * m->nrec, m->stream);
+        ++g_launches;
+        pending_old = -1;
+        return e == cudaSuccess ? FD_OK : cuda_fail(e, "receiver gather");
+    };
+    int s0 = 0;
+    if (m->tfuse == 2 && m->d.ndim == 3 && !lp && !img_grad && m->stall_stage < 0) {
+        for (; s0 + 2 <= nsteps; s0 += 2)
+            if (fd_status st = step_pair(m, pending_old))
+                return st;
+    }
+    if (fd_status st = flush_old())
+        return st;
+    nsteps -= s0;
     StepParams p{};
     p.stall_stage = m->stall_stage;
     p.lp_out = lp;
@@ -696,6 +778,59 @@ static fd_status step_n(fd_model *m, int nsteps, float *lp, const float *img_lp 
         ++m->n;
     }
     return flush_pending(m);
+}
+
+extern "C" fd_status fd_set_time_fusion(fd_model *m, int steps)
+{
+    NEED_MODEL(m);
+    if (steps != 1 && steps != 2)
+        return fail(FD_EINVAL, "fd_set_time_fusion: steps must be 1 or 2");
+    if (steps == 2 && m->d.ndim != 3)
+        return fail(FD_EINVAL, "fd_set_time_fusion: two fused steps need a 3D model");
+    if (steps == 2 && !m->xbuf[0]) {
+        const size_t bytes = m->pitched * sizeof(float);
+        float *b[2] = {nullptr, nullptr};
+        cudaError_t e = cudaMalloc((void **)&b[0], bytes);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&b[1], bytes);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b[0], 0, bytes, m->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b[1], 0, bytes, m->stream);
+        if (e != cudaSuccess) {
+            cudaFree(b[0]);
+            cudaFree(b[1]);
+            return cuda_fail(e, "fused-step buffers");
+        }
+        bool ok = true;
+        for (int i = 0; i < 2; ++i) {
+            ok = ok && make_map(&m->xhalo_map[i], b[i], 3, m->nx, m->ny, m->nz, m->px, kTX3 + 8, kTY3 + 8, kPlanes3);
+            ok = ok && make_map(&m->xtile_map[i], b[i], 3, m->nx, m->ny, m->nz, m->px, kTX3, kTY3, kPlanes3);
+            ok = ok && make_map(&m->xt2p1_map[i], b[i], 3, m->nx, m->ny, m->nz, m->px, 48, 48, 1);
+            ok = ok && make_map(&m->xt2e_map[i], b[i], 3, m->nx, m->ny, m->nz, m->px, 40, 40, 1);
+            ok = ok && make_map(&m->t2p1_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, 48, 48, 1);
+            ok = ok && make_map(&m->t2e_map[i], m->buf[i], 3, m->nx, m->ny, m->nz, m->px, 40, 40, 1);
+        }
+        ok = ok && make_map(&m->t2w_map, m->w, 3, m->nx, m->ny, m->nz, m->px, 40, 40, 1);
+        if (!ok) {
+            cudaFree(b[0]);
+            cudaFree(b[1]);
+            return fail(FD_ECUDA, "cuTensorMapEncodeTiled failed");
+        }
+        FD_CUDA(step3d_t2_prepare(), "fused-step kernel attributes");
+        m->xbuf[0] = b[0];
+        m->xbuf[1] = b[1];
+        // about six waves of one-CTA-per-SM launches, each CTA marching at least 32 planes
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+        const long long tiles = (long long)((m->nx + 31) / 32) * ((m->ny + 31) / 32);
+        long long bz = (long long)m->nz * tiles / (6LL * sms);
+        bz = std::max(32LL, std::min<long long>(bz, m->nz));
+        m->t2_nchunks = (int)((m->nz + bz - 1) / bz);
+        m->t2_bz = (m->nz + m->t2_nchunks - 1) / m->t2_nchunks;
+    }
+    m->tfuse = steps;
+    return FD_OK;
 }
 
 extern "C" fd_status fd_step(fd_model *m, int nsteps)

@@ -75,6 +75,33 @@ struct StepParams {
     int stall_stage = -1;     // test hook: CTA (0, 0) of the 3D step never issues this P stage (-1: none)
 };
 
+// Two fused time steps per launch (3D): a CTA of kT2Threads threads owns a 32 x 32
+// column and marches along z through bz planes.
+constexpr int kT2Threads = 416;
+
+struct T2Params {
+    float *out2, *out3;       // P^{n+1} and P^{n+2} destinations (pitched; neither input buffer)
+    const float *P0, *P1;     // levels n-1 and n (pitched; read by the receiver gathers)
+    const float *ax, *ay, *az;
+    float c1, c2, c3, c4;
+    int nx, ny, nz, px;
+    int bz;
+    int has_sponge;
+    int src_on0, src_on1, sx, sy, sz;   // source active in the first / second step
+    float amp0, amp1;                   // its amplitudes dt^2 S(t_n) / h^3, dt^2 S(t_{n+1}) / h^3
+    const int64_t *rec_idx;
+    int nrec;
+    float *trace_prev0;       // if set: trace_prev0[r] = P0[rec_idx[r]] (row owed for level n-1)
+    float *trace_prev1;       // if set: trace_prev1[r] = P1[rec_idx[r]] (row owed for level n)
+    int *err;
+};
+
+size_t step3d_t2_smem_bytes();
+cudaError_t step3d_t2_prepare();
+// tmP1: box 48 x 48 x 1 over level n; tmP0: box 40 x 40 x 1 over level n-1; tmW: 40 x 40 x 1 over w.
+cudaError_t launch_step3d_t2(const CUtensorMap &tmP1, const CUtensorMap &tmP0, const CUtensorMap &tmW,
+                             const T2Params &p, int nchunks, cudaStream_t s);
+
 size_t step3d_smem_bytes();
 cudaError_t step3d_prepare();
 int step3d_blocks_per_sm();

@@ -67,4 +67,15 @@ struct fd_model {
     int pending_row = -1;      // receiver row whose gather is still owed
 
     float *deriv[3] = {nullptr, nullptr, nullptr};   // Pxx, Pyy, Pzz of the unfused routines
+
+    // Two steps per launch (fd_set_time_fusion, 3D): the launch writes both new
+    // levels into two more buffers, which then trade places with buf[] (pointers
+    // and tensor maps together).
+    int tfuse = 1;
+    float *xbuf[2] = {nullptr, nullptr};
+    CUtensorMap xhalo_map[2], xtile_map[2];   // single-step maps over xbuf[i]
+    CUtensorMap t2p1_map[2], t2e_map[2];      // fused-step maps over buf[i]: 48x48x1 and 40x40x1 boxes
+    CUtensorMap xt2p1_map[2], xt2e_map[2];    // ... over xbuf[i]
+    CUtensorMap t2w_map;                      // 40x40x1 box over w
+    int t2_nchunks = 1, t2_bz = 1;
 };

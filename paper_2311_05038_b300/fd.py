@@ -44,7 +44,7 @@ EXPORTS = [
     "fd_adjoint_segment", "fd_gather_traces_async", "fd_debug_poison_padding", "fd_step_image",
     "fd_inject_receivers_image", "fd_step_lp_n", "fd_adjoint_backward", "fd_debug_stall_stage",
     "fd_set_stream", "fd_stream_create", "fd_stream_destroy", "fd_velocity_from_slowness",
-    "fd_gradient_from_image",
+    "fd_gradient_from_image", "fd_set_time_fusion",
 ]
 
 
@@ -130,6 +130,7 @@ _SIGS = {
     "fd_stream_destroy": (_i, [_vp]),
     "fd_velocity_from_slowness": (_i, [_vp, _vp, _sz, _vp]),
     "fd_gradient_from_image": (_i, [_vp, _i, _vp, _vp, _sz, _vp]),
+    "fd_set_time_fusion": (_i, [_vp, _i]),
     "fd_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -200,6 +201,10 @@ def fd_model_create_dev(desc: fd_grid_desc, v_dev, stream=None) -> int:
 
 def fd_model_destroy(m: int):
     _check(_lib.fd_model_destroy(m), "fd_model_destroy")
+
+
+def fd_set_time_fusion(m: int, steps: int):
+    _check(_lib.fd_set_time_fusion(m, int(steps)), "fd_set_time_fusion")
 
 
 def fd_set_stream(m: int, stream):
@@ -514,6 +519,9 @@ class Model:
 
     def run_shot(self, nt, traces_dev=None):
         fd_run_shot(self.handle, nt, traces_dev)
+
+    def set_time_fusion(self, steps):
+        fd_set_time_fusion(self.handle, steps)
 
     def step(self, n):
         fd_step(self.handle, n)

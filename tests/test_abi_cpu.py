@@ -103,6 +103,7 @@ def test_null_arguments_are_einval(fdlib):
     assert fdlib._lib.fd_set_stream(None, None) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_stream_create(0, None, None) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_stream_destroy(None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_set_time_fusion(None, 2) == fdlib.FD_EINVAL
 
 
 @pytest.mark.skipif(cuda_available(), reason="checks the no-device error path")
