@@ -145,6 +145,23 @@ bool fdk::make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int 
     return r == CUDA_SUCCESS;
 }
 
+// A rank-3 FP32 tensor map with explicit extents (x fastest) and byte strides of
+// the two outer dimensions, for views whose outer axes are permuted.
+bool fdk::make_map_strided(CUtensorMap *map, float *base, const uint64_t (&dims)[3], const uint64_t (&strides)[2],
+                           const uint32_t (&box)[3])
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return false;
+    cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+    cuuint64_t st[2] = {strides[0], strides[1]};
+    cuuint32_t b[3] = {box[0], box[1], box[2]};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, d, st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------------ model
 
 static fd_status validate_desc(const fd_grid_desc *d)

@@ -73,6 +73,9 @@ struct StepParams {
     float *img_grad;          //   both dense [nz][ny][nx]
     int *err;                 // device error word
     int stall_stage = -1;     // test hook: CTA (0, 0) of the 3D step never issues this P stage (-1: none)
+    int deriv_axis = -1;      // 0, 1, 2: write only the x / y / z second derivative of P to out (3D)
+    long long out_sy = 0;     // derivative modes: element strides of out along the kernel's y and z
+    long long out_sz = 0;     //   (0: the layout of P, px and ny * px)
 };
 
 // Two fused time steps per launch (3D): a CTA of kT2Threads threads owns a 32 x 32
@@ -126,6 +129,10 @@ cudaError_t launch_compute_w(const float *v, float *w, int nx, size_t rows, int 
 // rank 3 ([nz][ny][px], extents nx, ny, nz), with box bx x by (x bz planes).
 bool make_map(CUtensorMap *map, float *base, int ndim, int nx, int ny, int nz, int px, int bx, int by,
               int bz = 1);
+// Rank-3 FP32 tensor map with explicit extents (x fastest), byte strides of the
+// two outer dimensions (multiples of 16) and box.
+bool make_map_strided(CUtensorMap *map, float *base, const uint64_t (&dims)[3], const uint64_t (&strides)[2],
+                      const uint32_t (&box)[3]);
 // Record a message for fd_last_error() and return st.
 fd_status fail(fd_status st, const char *fmt, ...);
 fd_status cuda_fail(cudaError_t e, const char *what);

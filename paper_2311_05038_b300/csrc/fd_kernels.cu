@@ -53,8 +53,12 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 // prm.lp_out; MODE 2 also adds Pn * prm.img_lp to prm.img_grad.  Both serve the
 // adjoint's imaging condition; MODE 0 is the plain step.  MODE 3 is the plain
 // step with the failure-path test hook (prm.stall_stage), kept out of MODE 0.
+// MODES 4, 5, 6 are the paper's unfused derivative routines (fd_pxx, fd_pyy,
+// fd_pzz): they stream P through the same ring and write only
+// sum_k c_k (P[+k] + P[-k] - 2P) along x, y or z to prm.out, with no Pold or w
+// loads.
 template <int TX, int TY, int SP, int ST, int G, int MODE>
-__global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
+__global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
 {
@@ -75,11 +79,13 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     static_assert(kPlanes3 == 2, "bodies compute the two planes of a stage");
     static_assert(SP >= 4, "P ring must hold stages i+2 .. i+4 and run ahead");
     static_assert(ST >= 2, "T ring must run ahead");
+    constexpr bool DERIV = MODE >= 4;   // one axis's second derivative only
+    constexpr int DAXIS = MODE - 4;     // 0: x, 1: y, 2: z
 
     extern __shared__ __align__(128) unsigned char smem[];
     float *sP = reinterpret_cast<float *>(smem);
-    float *sT = sP + SP * PST;
-    uint64_t *fullP = reinterpret_cast<uint64_t *>(sT + ST * TST);
+    float *sT = sP + SP * PST;   // the derivative modes have no T ring
+    uint64_t *fullP = reinterpret_cast<uint64_t *>(sT + (DERIV ? 0 : ST * TST));
     uint64_t *fullT = fullP + SP;
     unsigned *relP = reinterpret_cast<unsigned *>(fullT + ST);
     unsigned *relT = relP + SP;
@@ -153,8 +159,10 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
         prefetch_tensormap(&tmW);
         for (int k = 0; k < min(SP, nPS); ++k)
             issueP(k, k);
-        for (int t = 0; t < min(ST, nbh); ++t)
-            issueT(t, t);
+        if constexpr (!DERIV) {
+            for (int t = 0; t < min(ST, nbh); ++t)
+                issueT(t, t);
+        }
     }
 
     gather_prev_row(prm);
@@ -184,6 +192,10 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     const bool store_any = row_ok && x < prm.nx;
     float *const out_col = prm.out + ((size_t)z0 * prm.ny + y) * prm.px + x;
     const size_t plane_stride = (size_t)prm.ny * prm.px;
+    // derivative modes may write a permuted view (the kernel's y and z swapped)
+    const size_t deriv_sy = DERIV && prm.out_sy ? (size_t)prm.out_sy : (size_t)prm.px;
+    const size_t deriv_sz = DERIV && prm.out_sz ? (size_t)prm.out_sz : plane_stride;
+    float *const deriv_col = prm.out + (size_t)z0 * deriv_sz + (size_t)y * deriv_sy + x;
 
     // z queue, advanced G bodies (2G planes) at a time: in the r-th body of a
     // group, Q[i + 2r] holds relative plane j + i.
@@ -212,6 +224,65 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     // L'P in packed FP32 in the same rounding order as update_point<3>.
     auto plane = [&](int j, const float *pl, const float *tb, float azv, auto qo) {
         constexpr int O = decltype(qo)::value;   // Q index of this plane's centre
+        if constexpr (DERIV) {
+            const float4 &pc = Q[O];
+            if constexpr (DAXIS == 0) {
+                const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
+                const float4 xp = *reinterpret_cast<const float4 *>(pl + 4);
+                const float xa[12] = {xm.x, xm.y, xm.z, xm.w, pc.x, pc.y, pc.z, pc.w, xp.x, xp.y, xp.z, xp.w};
+                float2 acc[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 p2 = half2of(pc, h);
+                    float2 a2;
+#pragma unroll
+                    for (int k = 1; k <= 4; ++k) {
+                        const float2 d = __ffma2_rn(make_float2(-2.0f, -2.0f), p2, xpair2(xa, h, k));
+                        const float2 ck = k == 1 ? C1 : k == 2 ? C2 : k == 3 ? C3 : C4;
+                        a2 = k == 1 ? __fmul2_rn(ck, d) : __ffma2_rn(ck, d, a2);
+                    }
+                    acc[h] = a2;
+                }
+                float *dst = deriv_col + (size_t)j * deriv_sz;
+                if (store_vec)
+                    *reinterpret_cast<float4 *>(dst) = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+                else if (store_any)
+                    store4(dst, acc, prm.nx - x);
+                return;
+            } else {
+                float4 mk[4], pk[4];
+#pragma unroll
+                for (int k = 1; k <= 4; ++k) {
+                    if constexpr (DAXIS == 1) {
+                        mk[k - 1] = *reinterpret_cast<const float4 *>(pl - k * HX);
+                        pk[k - 1] = *reinterpret_cast<const float4 *>(pl + k * HX);
+                    } else {
+                        mk[k - 1] = Q[O - k];
+                        pk[k - 1] = Q[O + k];
+                    }
+                }
+                float2 acc[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 p2 = half2of(pc, h);
+                    float2 a2;
+#pragma unroll
+                    for (int k = 1; k <= 4; ++k) {
+                        const float2 sk = __fadd2_rn(half2of(pk[k - 1], h), half2of(mk[k - 1], h));
+                        const float2 d = __ffma2_rn(make_float2(-2.0f, -2.0f), p2, sk);
+                        const float2 ck = k == 1 ? C1 : k == 2 ? C2 : k == 3 ? C3 : C4;
+                        a2 = k == 1 ? __fmul2_rn(ck, d) : __ffma2_rn(ck, d, a2);
+                    }
+                    acc[h] = a2;
+                }
+                float *dst = deriv_col + (size_t)j * deriv_sz;
+                if (store_vec)
+                    *reinterpret_cast<float4 *>(dst) = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+                else if (store_any)
+                    store4(dst, acc, prm.nx - x);
+                return;
+            }
+        }
         const float4 xm = *reinterpret_cast<const float4 *>(pl - 4);
         const float4 xc = *reinterpret_cast<const float4 *>(pl);
         const float4 xp = *reinterpret_cast<const float4 *>(pl + 4);
@@ -289,7 +360,13 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
     auto body = [&](int i, auto rot) {
         constexpr int R = decltype(rot)::value;
         // fast path: both stages already landed; else bounded waits
-        if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[sn], phn) & mbar_try_wait(&fullT[st], pht))) {
+        if constexpr (DERIV) {
+            if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[sn], phn))) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&fullP[sn], phn, &s_abort));
+                if (!ok)
+                    return;
+            }
+        } else if (!__all_sync(0xffffffffu, mbar_try_wait(&fullP[sn], phn) & mbar_try_wait(&fullT[st], pht))) {
             ok = __all_sync(0xffffffffu, mbar_wait(&fullP[sn], phn, &s_abort) &&
                                              mbar_wait(&fullT[st], pht, &s_abort));
             if (!ok)
@@ -309,7 +386,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, kMinBlocks3)
         plane(j, pl, tb, a0v, std::integral_constant<int, 4 + 2 * R>{});
         if (j + 1 < nb)
             plane(j + 1, pl + PBOX, tb + TBOX, a1v, std::integral_constant<int, 5 + 2 * R>{});
-        release(i + 2, sx, i, st);
+        release(i + 2, sx, DERIV ? -1 : i, st);
         if (++sn == SP) {
             sn = 0;
             phn ^= 1;
@@ -486,6 +563,14 @@ size_t step3d_smem_bytes()
            (kStagesP3 + kStagesT3) * (sizeof(uint64_t) + sizeof(unsigned));
 }
 
+// The derivative modes keep only the P ring.
+static size_t deriv3d_smem_bytes()
+{
+    constexpr int PBOX = (kTX3 + 8) * (kTY3 + 8);
+    return (size_t)(kStagesP3 * kPlanes3 * PBOX) * sizeof(float) +
+           (kStagesP3 + kStagesT3) * (sizeof(uint64_t) + sizeof(unsigned));
+}
+
 cudaError_t step3d_prepare()
 {
     const int bytes = (int)step3d_smem_bytes();
@@ -496,6 +581,12 @@ cudaError_t step3d_prepare()
         e = cudaFuncSetAttribute(FD_STEP3D(2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(FD_STEP3D(3), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(4), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(5), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(FD_STEP3D(6), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
@@ -513,7 +604,13 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
 {
     const int tiles = ((p.nx + kTX3 - 1) / kTX3) * ((p.ny + kTY3 - 1) / kTY3);
     dim3 grid(tiles, nchunks);
-    if (p.lp_out)
+    if (p.deriv_axis == 0)
+        FD_STEP3D(4)<<<grid, kThreads3, deriv3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else if (p.deriv_axis == 1)
+        FD_STEP3D(5)<<<grid, kThreads3, deriv3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else if (p.deriv_axis == 2)
+        FD_STEP3D(6)<<<grid, kThreads3, deriv3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    else if (p.lp_out)
         FD_STEP3D(1)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     else if (p.img_grad)
         FD_STEP3D(2)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);

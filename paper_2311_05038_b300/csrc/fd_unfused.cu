@@ -224,6 +224,75 @@ static UnfusedParams unfused_params(fd_model *m)
     return p;
 }
 
+// One 3D derivative routine through the step kernel's derivative mode: the haloed
+// P ring of the fused step streams level n, and only sum_k c_k (P[+k] + P[-k] - 2P)
+// along the axis is written, to deriv[axis].  x and z take their neighbours as
+// the fused step does (from the ring plane and from the thread's z queue).  y
+// runs as a z derivative over a view with y and z swapped (its tensor map and
+// output strides permuted), so that it too marches with a register queue.
+static cudaError_t launch_deriv3d(fd_model *m, int axis)
+{
+    if (axis == 1) {
+        const uint64_t dims[3] = {(uint64_t)m->nx, (uint64_t)m->nz, (uint64_t)m->ny};
+        const uint64_t strides[2] = {(uint64_t)m->ny * m->px * 4, (uint64_t)m->px * 4};
+        const uint32_t halo[3] = {kTX3 + 8, kTY3 + 8, kPlanes3}, tile[3] = {kTX3, kTY3, kPlanes3};
+        CUtensorMap tmP, tmT;
+        if (!make_map_strided(&tmP, m->buf[m->cur], dims, strides, halo) ||
+            !make_map_strided(&tmT, m->buf[m->cur ^ 1], dims, strides, tile))
+            return cudaErrorInvalidValue;
+        float w4[4];
+        fd_stencil_weights(w4);
+        StepParams p{};
+        p.deriv_axis = 2;
+        p.out = m->deriv[1];
+        p.P = m->buf[m->cur];
+        p.ax = m->ax;
+        p.ay = m->ay;
+        p.az = m->az;
+        p.c1 = w4[0];
+        p.c2 = w4[1];
+        p.c3 = w4[2];
+        p.c4 = w4[3];
+        p.nx = m->nx;
+        p.ny = m->nz;                 // the view's y is the grid's z
+        p.nz = m->ny;                 // and its z (the march axis) the grid's y
+        p.px = m->px;
+        p.out_sy = (long long)m->ny * m->px;
+        p.out_sz = m->px;
+        p.err = m->d_err;
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+        const long long tiles = (long long)((m->nx + kTX3 - 1) / kTX3) * ((m->nz + kTY3 - 1) / kTY3);
+        const long long slots = (long long)sms * step3d_blocks_per_sm();
+        long long bz = (long long)m->ny * tiles / (6 * slots);
+        bz = std::max(32LL, std::min<long long>(bz, m->ny));
+        const int nchunks = (int)((m->ny + bz - 1) / bz);
+        p.bz = (m->ny + nchunks - 1) / nchunks;
+        return launch_step3d(tmP, tmT, tmT, p, nchunks, m->stream);
+    }
+    float w4[4];
+    fd_stencil_weights(w4);
+    StepParams p{};
+    p.deriv_axis = axis;
+    p.out = m->deriv[axis];
+    p.P = m->buf[m->cur];
+    p.ax = m->ax;
+    p.ay = m->ay;
+    p.az = m->az;
+    p.c1 = w4[0];
+    p.c2 = w4[1];
+    p.c3 = w4[2];
+    p.c4 = w4[3];
+    p.nx = m->nx;
+    p.ny = m->ny;
+    p.nz = m->nz;
+    p.px = m->px;
+    p.bz = m->bz;
+    p.err = m->d_err;
+    const int c = m->cur;
+    return launch_step3d(m->halo_map[c], m->tile_map[c ^ 1], m->w_map, p, m->nchunks, m->stream);
+}
+
 extern "C" fd_status fd_routine(fd_model *m, int routine)
 {
     if (!m)
@@ -241,11 +310,20 @@ extern "C" fd_status fd_routine(fd_model *m, int routine)
     cudaError_t e = cudaSuccess;
     switch (routine) {
     case FD_ROUTINE_PXX:
+        if (m->d.ndim == 3) {
+            e = launch_deriv3d(m, 0);
+            break;
+        }
         p.out = m->deriv[0];
         d2x_kernel<<<blocks, 256, 0, m->stream>>>(p);
         break;
     case FD_ROUTINE_PYY:
     case FD_ROUTINE_PZZ: {
+        if (m->d.ndim == 3) {
+            // the fused step's TMA ring, writing one axis's derivative only
+            e = launch_deriv3d(m, routine == FD_ROUTINE_PYY ? 1 : 2);
+            break;
+        }
         const bool y = routine == FD_ROUTINE_PYY;
         p.out = m->deriv[y ? 1 : 2];
         const int qx = (m->nx + 3) / 4;
