@@ -141,6 +141,46 @@ def percentile(values, q):
     return float(v[k])
 
 
+# ------------------------------------------------------------------ scheduling policy
+
+def admit_in_order(waiting, free_slots, bypassed, max_bypass, try_admit):
+    """Admit from ``waiting`` (a list in arrival order, modified in place) into at
+    most ``free_slots`` slots.  ``try_admit(request)`` returns the admitted entry or
+    None when the request does not fit yet; a request that does not fit lets later
+    ones pass it until ``max_bypass`` of them have (``bypassed`` counts them for the
+    current head and is returned updated), after which nothing passes it.
+    Returns (admitted entries, bypassed)."""
+    out = []
+    i = 0
+    while i < len(waiting) and len(out) < free_slots:
+        if i > 0 and bypassed >= max_bypass:
+            break
+        a = try_admit(waiting[i])
+        if a is None:
+            i += 1
+            continue
+        del waiting[i]
+        bypassed = bypassed + 1 if i > 0 else 0
+        out.append(a)
+    return out, bypassed
+
+
+def rank_active(active, policy, slack=2.0, rate=300e9):
+    """Active shots in priority order.  Each entry needs ``arrival``, ``rid``,
+    ``npoints``, ``nt`` and ``work_left``.  "age": oldest first; "oldest+srpt":
+    the oldest, then least remaining work; "deadline": earliest arrival + slack x
+    stand-alone time (npoints x nt / rate)."""
+    if policy == "age":
+        return sorted(active, key=lambda a: (a.arrival, a.rid))
+    if policy == "oldest+srpt":
+        oldest = min(active, key=lambda a: (a.arrival, a.rid))
+        rest = sorted((a for a in active if a is not oldest), key=lambda a: (a.work_left, a.rid))
+        return [oldest] + rest
+    if policy == "deadline":
+        return sorted(active, key=lambda a: (a.arrival + slack * a.npoints * a.nt / rate, a.rid))
+    raise ValueError(f"unknown policy {policy!r}")
+
+
 # ------------------------------------------------------------------ server
 
 @dataclass
@@ -152,9 +192,26 @@ class _Active:
     remaining: int              # steps not yet issued
     inflight: collections.deque = field(default_factory=collections.deque)   # (event, steps)
 
+    @property
     def work_left(self) -> int:
         """Grid-point updates not yet completed."""
         return (self.remaining + sum(k for _, k in self.inflight)) * int(self.req.shot.npoints)
+
+    @property
+    def arrival(self):
+        return self.req.arrival
+
+    @property
+    def rid(self):
+        return self.req.rid
+
+    @property
+    def npoints(self):
+        return int(self.req.shot.npoints)
+
+    @property
+    def nt(self):
+        return int(self.req.shot.nt)
 
 
 class Server:
@@ -252,15 +309,7 @@ class Server:
 
     def _rank(self, active):
         """Active shots in priority order under the server's policy."""
-        if self.policy == "age":
-            return sorted(active, key=lambda a: (a.req.arrival, a.req.rid))
-        if self.policy == "oldest+srpt":
-            oldest = min(active, key=lambda a: (a.req.arrival, a.req.rid))
-            rest = sorted((a for a in active if a is not oldest), key=lambda a: (a.work_left(), a.req.rid))
-            return [oldest] + rest
-        # deadline: a shot is due slack times its stand-alone time after it arrived
-        return sorted(active, key=lambda a: (a.req.arrival + self.slack * a.req.shot.npoints * a.req.shot.nt
-                                             / self.rate, a.req.rid))
+        return rank_active(active, self.policy, self.slack, self.rate)
 
     def _reprioritise(self, active):
         """Priorities from the device's greatest down to 0 (the default) in rank
@@ -288,17 +337,10 @@ class Server:
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             progressed = False
-            i = 0
-            while i < len(waiting) and len(active) < self.max_active:
-                if i > 0 and bypassed >= self.max_bypass:
-                    break
-                a = self._admit(waiting[i], now)
-                if a is None:             # does not fit yet: later requests may pass it
-                    i += 1
-                    continue
-                del waiting[i]
-                bypassed = bypassed + 1 if i > 0 else 0
-                active.append(a)
+            admitted, bypassed = admit_in_order(waiting, self.max_active - len(active), bypassed,
+                                                self.max_bypass, lambda q: self._admit(q, now))
+            if admitted:
+                active.extend(admitted)
                 progressed = True
             if progressed:
                 self._reprioritise(active)

@@ -81,3 +81,44 @@ def test_percentile_nearest_rank():
     v = list(range(1, 101))
     assert serving.percentile(v, 50) == 50 and serving.percentile(v, 99) == 99
     assert serving.percentile([3.0], 99) == 3.0
+
+
+# ------------------------------------------------------------------ scheduling policy
+
+class Req:
+    def __init__(self, rid, arrival, npoints=1000, nt=100, work_left=None, fits=True):
+        self.rid, self.arrival, self.npoints, self.nt = rid, arrival, npoints, nt
+        self.work_left = npoints * nt if work_left is None else work_left
+        self.fits = fits
+
+
+def test_admission_keeps_arrival_order_when_everything_fits():
+    waiting = [Req(i, 0.1 * i) for i in range(5)]
+    got, byp = serving.admit_in_order(waiting, 3, 0, 8, lambda q: q if q.fits else None)
+    assert [q.rid for q in got] == [0, 1, 2] and [q.rid for q in waiting] == [3, 4] and byp == 0
+
+
+def test_admission_lets_fitting_requests_pass_a_blocked_head_up_to_the_bound():
+    waiting = [Req(0, 0.0, fits=False)] + [Req(i, 0.1 * i) for i in range(1, 6)]
+    got, byp = serving.admit_in_order(waiting, 10, 0, 3, lambda q: q if q.fits else None)
+    assert [q.rid for q in got] == [1, 2, 3] and byp == 3          # three passed, then the head blocks
+    assert waiting[0].rid == 0
+    got, byp = serving.admit_in_order(waiting, 10, byp, 3, lambda q: q if q.fits else None)
+    assert got == [] and byp == 3                                  # nothing more passes it
+    waiting[0].fits = True
+    got, byp = serving.admit_in_order(waiting, 1, byp, 3, lambda q: q if q.fits else None)
+    assert [q.rid for q in got] == [0] and byp == 0                # the head goes first, the count resets
+
+
+def test_priority_rankings():
+    a = Req(0, 0.0, npoints=10**6, nt=2000)     # old, big
+    b = Req(1, 0.5, npoints=10**3, nt=100)      # newer, tiny
+    c = Req(2, 0.2, npoints=10**5, nt=500, work_left=10)
+    assert [r.rid for r in serving.rank_active([a, b, c], "age")] == [0, 2, 1]
+    assert [r.rid for r in serving.rank_active([a, b, c], "oldest+srpt")] == [0, 2, 1]
+    # deadline: arrival + 2 x npoints x nt / 300e9 -> a: 0.0133, b: 0.5, c: 0.2003
+    assert [r.rid for r in serving.rank_active([a, b, c], "deadline")] == [0, 2, 1]
+    late_big = Req(3, 0.0, npoints=10**8, nt=2000)   # due 1.33 s after arrival
+    assert [r.rid for r in serving.rank_active([late_big, b], "deadline")] == [1, 3]
+    with pytest.raises(ValueError):
+        serving.rank_active([a], "fifo")
