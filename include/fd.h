@@ -339,10 +339,15 @@ fd_status fd_step_unfused(fd_model *m, int nsteps);
 typedef struct fd_batch fd_batch;
 
 typedef struct fd_batch_tuning {
-    int tile;              /* tile shape: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 (x by z) */
-    int steps_per_launch;  /* time steps per persistent launch, >= 1                       */
-    int ctas_per_sm;       /* resident CTAs per SM, 0 = as many as fit                      */
-    int group_mb;          /* L2 budget per shot group in MB, 0 = all shots in one group    */
+    int tile;              /* schedule and tile shape (x by z): one persistent launch with
+                              0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 tiles; or one ordinary
+                              launch per time step over all of a group's shots (tensor maps
+                              in the launch parameters, up to 64 shots a launch) with
+                              3 = 64 x 16, 4 = 64 x 32 tiles                                */
+    int steps_per_launch;  /* time steps per persistent launch, >= 1 (persistent only)      */
+    int ctas_per_sm;       /* resident CTAs per SM, 0 = as many as fit (persistent only)    */
+    int group_mb;          /* L2 budget per shot group in MB, 0 = all shots in one group;
+                              the groups run one after another                              */
 } fd_batch_tuning;
 
 /* Build a batch over nmodels 2D models on the same device (FD_EINVAL for 3D
@@ -356,7 +361,7 @@ fd_status fd_batch_get_tuning(fd_batch *b, fd_batch_tuning *t);
  * nsteps_each is NULL), exactly as fd_step would, traces included.  Blocks
  * until done; returns FD_ETIMEOUT if a bounded device wait gave up. */
 fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each);
-/* Test hook for the failure path: from the next fd_batch_step on, work item
+/* Test hook for the failure path (persistent schedules, tiles 0-2): from the next fd_batch_step on, work item
  * stalled_item (0-based in the batch's (shot, tile) order; -1 clears it) never
  * runs, so its neighbours' bounded waits run out and the call returns
  * FD_ETIMEOUT with the context still usable.  After FD_ETIMEOUT the shots'

@@ -360,6 +360,117 @@ __global__ void __launch_bounds__(TX / 4 * TZ + 32) batch2d_kernel(const BatchPa
     }
 }
 
+// ---------------------------------------------------------------- wide schedule
+//
+// One ordinary launch per time step over the tiles of up to kWideMax shots, a
+// CTA per (shot, tile).  Everything a CTA needs -- its shot's three tensor maps,
+// pointers, extents, source and receivers -- travels in the launch's parameter
+// block, so a CTA finds its shot by a binary search over the shots' first tiles
+// in parameter space and issues its TMA loads at once, with no dependent global
+// loads before them.  The per-tile arithmetic is the single-shot 2D step's
+// (stencil.cuh), so shots are bitwise the same as alone.  No CTA waits on
+// another: the launch boundary orders the steps.
+
+constexpr int kWideMax = 64;
+
+struct WideShot {
+    float *out;               // Pn destination (the shot's Pold buffer)
+    const float *P;           // level n (read by the receiver gather)
+    const float *ax, *az;
+    float *trace_prev;        // the row owed for level n, or null
+    const int64_t *rec_idx;
+    int nrec;
+    int nx, nz, px;
+    int tiles_x;
+    int tile_begin;           // first CTA of this shot
+    int has_sponge, src_on, sx, sz;
+    float src_amp;
+};
+
+struct WideParams {
+    CUtensorMap halo[kWideMax];   // haloed P box over level n
+    CUtensorMap tile[kWideMax];   // Pold tile box
+    CUtensorMap wmap[kWideMax];
+    WideShot shot[kWideMax];
+    int nshots;
+    float c1, c2, c3, c4;
+    int *err;
+};
+
+template <int TX, int TZ>
+__global__ void __launch_bounds__(TX / 4 * TZ) wide2d_kernel(const __grid_constant__ WideParams prm)
+{
+    constexpr int QX = TX / 4;
+    constexpr int HX = TX + 8;
+    constexpr int HZ = TZ + 8;
+    constexpr uint32_t BYTES = (HX * HZ + 2 * TX * TZ) * 4;
+    __shared__ __align__(128) float sP[HX * HZ];
+    __shared__ __align__(128) float sO[TX * TZ];
+    __shared__ __align__(128) float sW[TX * TZ];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+
+    // the shot of this CTA: the last s with shot[s].tile_begin <= blockIdx.x
+    int lo = 0, hi = prm.nshots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prm.shot[mid].tile_begin <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int s = lo;
+    const WideShot &sh = prm.shot[s];
+    const int t = blockIdx.x - sh.tile_begin;
+    const int x0 = (t % sh.tiles_x) * TX;
+    const int z0 = (t / sh.tiles_x) * TZ;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, BYTES);
+        tma_load_2d(sP, &prm.halo[s], &bar, x0 - 4, z0 - 4);
+        tma_load_2d(sO, &prm.tile[s], &bar, x0, z0);
+        tma_load_2d(sW, &prm.wmap[s], &bar, x0, z0);
+    }
+    // receivers of this shot's previous step, spread over the shot's CTAs
+    if (sh.trace_prev) {
+        const int ntiles = sh.tiles_x * ((sh.nz + TZ - 1) / TZ);
+        for (int r = t * blockDim.x + tid; r < sh.nrec; r += ntiles * blockDim.x)
+            sh.trace_prev[r] = sh.P[sh.rec_idx[r]];
+    }
+
+    const int tx = tid % QX;
+    const int tz = tid / QX;
+    const int x = x0 + 4 * tx;
+    const int z = z0 + tz;
+    float axv[4] = {0.f, 0.f, 0.f, 0.f};
+    float azv = 0.f;
+    if (sh.has_sponge) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            axv[e] = x + e < sh.px ? sh.ax[x + e] : 0.f;
+        azv = z < sh.nz ? sh.az[z] : 0.f;
+    }
+    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
+    if (!ok) {
+        if (tid == 0)
+            raise_error(prm.err, &s_abort, kDevErrTimeout);
+        return;
+    }
+    float2 r[2], lp[2];
+    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
+    if (sh.src_on && z == sh.sz && (unsigned)(sh.sx - x) < 4u)
+        add_source4(r, sh.sx - x, sh.src_amp);
+    if (z < sh.nz && x < sh.nx)
+        store4(sh.out + (size_t)z * sh.px + x, r, sh.nx - x);
+}
+
 // Compiled tile variants: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16.
 constexpr int kBatchStages = 3;
 struct Variant {
@@ -367,6 +478,7 @@ struct Variant {
     const void *fn;
     int threads;
     size_t smem;
+    bool wide = false;   // one launch per time step (wide2d_kernel) instead of the persistent kernel
 };
 
 template <int TX, int TZ>
@@ -379,6 +491,14 @@ static Variant variant()
     return Variant{TX, TZ, (const void *)batch2d_kernel<TX, TZ, kBatchStages>, TX / 4 * TZ + 32, smem};
 }
 
+template <int TX, int TZ>
+static Variant wide_variant()
+{
+    return Variant{TX, TZ, (const void *)wide2d_kernel<TX, TZ>, TX / 4 * TZ, 0, true};
+}
+
+// Tile variants: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 (persistent kernel);
+// 3 = 64 x 16, 4 = 64 x 32 (one launch per time step).
 static Variant get_variant(int tile)
 {
     switch (tile) {
@@ -386,6 +506,10 @@ static Variant get_variant(int tile)
         return variant<64, 32>();
     case 2:
         return variant<128, 16>();
+    case 3:
+        return wide_variant<64, 16>();
+    case 4:
+        return wide_variant<64, 32>();
     default:
         return variant<64, 16>();
     }
@@ -413,6 +537,8 @@ struct fd_batch {
     int nitems = 0, ngroups = 0, grid = 0;
     cudaGraphExec_t exec = nullptr;
     std::vector<ShotDesc> shots;   // host copy (tensor maps, pointers)
+    std::vector<int> group_shot;   // first shot of each group, then the shot count
+    WideParams wide{};             // parameter block of the wide schedule's launches
     int stall_item = -1;           // fd_batch_set_fault
 };
 
@@ -443,6 +569,7 @@ static fd_status build_tables(fd_batch *b)
     std::vector<BatchItem> items;
     std::vector<BatchRec> recs;
     std::vector<int> group{0};
+    b->group_shot.assign(1, 0);
     const double budget = b->tun.group_mb > 0 ? b->tun.group_mb * 1048576.0 : 1e300;
     double in_group = 0.0;
     b->shots.assign(b->models.size(), ShotDesc{});
@@ -468,6 +595,7 @@ static fd_status build_tables(fd_batch *b)
         const double bytes = 3.0 * m->pitched * sizeof(float);
         if (s > 0 && in_group + bytes > budget) {
             group.push_back((int)items.size());
+            b->group_shot.push_back((int)s);
             in_group = 0.0;
         }
         in_group += bytes;
@@ -499,6 +627,7 @@ static fd_status build_tables(fd_batch *b)
             }
     }
     group.push_back((int)items.size());
+    b->group_shot.push_back((int)b->models.size());
     b->nitems = (int)items.size();
     b->ngroups = (int)group.size() - 1;
     FD_CUDA(cudaMalloc((void **)&b->d_shots, b->shots.size() * sizeof(ShotDesc)), "batch allocation");
@@ -511,6 +640,10 @@ static fd_status build_tables(fd_batch *b)
         FD_CUDA(cudaMemcpy(b->d_recs, recs.data(), recs.size() * sizeof(BatchRec), cudaMemcpyHostToDevice), "batch upload");
     FD_CUDA(cudaMemcpy(b->d_group, group.data(), group.size() * sizeof(int), cudaMemcpyHostToDevice), "batch upload");
 
+    if (v.wide) {
+        b->built = true;   // the wide schedule needs only the descriptors and the groups
+        return FD_OK;
+    }
     // resident grid
     FD_CUDA(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem), "kernel attributes");
     int per_sm = 0, sms = 0;
@@ -582,7 +715,7 @@ extern "C" fd_status fd_batch_set_tuning(fd_batch *b, const fd_batch_tuning *t)
 {
     if (!b || !t)
         return fail(FD_EINVAL, "fd_batch_set_tuning: NULL argument");
-    if (t->tile < 0 || t->tile > 2 || t->steps_per_launch < 1 || t->ctas_per_sm < 0 || t->group_mb < 0)
+    if (t->tile < 0 || t->tile > 4 || t->steps_per_launch < 1 || t->ctas_per_sm < 0 || t->group_mb < 0)
         return fail(FD_EINVAL, "fd_batch_set_tuning: value out of range");
     const bool same = t->tile == b->tun.tile && t->ctas_per_sm == b->tun.ctas_per_sm && t->group_mb == b->tun.group_mb;
     b->tun = *t;
@@ -645,6 +778,103 @@ static fd_status capture_graph(fd_batch *b, const BatchParams &p)
     return FD_OK;
 }
 
+// The wide schedule: group by group, one launch per time step over the tiles of
+// up to kWideMax of the group's shots that still have steps to go.  The host
+// keeps each shot's level parity, step counter and owed receiver row; the
+// launch gathers the owed rows of its shots, and the rows still owed at the end
+// are gathered by one small launch per shot.
+static fd_status run_wide(fd_batch *b, const std::vector<int> &target)
+{
+    const Variant v = get_variant(b->tun.tile);
+    float w4[4];
+    fd_stencil_weights(w4);
+    WideParams &p = b->wide;
+    p.c1 = w4[0];
+    p.c2 = w4[1];
+    p.c3 = w4[2];
+    p.c4 = w4[3];
+    p.err = b->d_err;
+    const size_t ns = b->models.size();
+    std::vector<int> pending(ns, -1), done(ns, 0);
+    for (size_t g = 0; g + 1 < b->group_shot.size(); ++g) {
+        const int sb = b->group_shot[g], se = b->group_shot[g + 1];
+        int kmax = 0;
+        for (int s = sb; s < se; ++s)
+            kmax = std::max(kmax, target[s]);
+        for (int k = 0; k < kmax; ++k) {
+            for (int s0 = sb; s0 < se;) {
+                int n = 0, tiles = 0;
+                std::vector<int> in;
+                for (; s0 < se && n < kWideMax; ++s0) {
+                    if (done[s0] >= target[s0])
+                        continue;
+                    fd_model *m = b->models[s0];
+                    const ShotDesc &d = b->shots[s0];
+                    const int c = m->cur;
+                    p.halo[n] = d.halo[c];
+                    p.tile[n] = d.tile[c ^ 1];
+                    p.wmap[n] = d.wmap;
+                    WideShot &w = p.shot[n];
+                    w.out = m->buf[c ^ 1];
+                    w.P = m->buf[c];
+                    w.ax = m->ax;
+                    w.az = m->az;
+                    w.trace_prev = pending[s0] >= 0 ? m->traces + (size_t)pending[s0] * m->nrec : nullptr;
+                    w.rec_idx = m->d_rec;
+                    w.nrec = m->nrec;
+                    w.nx = m->nx;
+                    w.nz = m->nz;
+                    w.px = m->px;
+                    w.tiles_x = (m->nx + v.tx - 1) / v.tx;
+                    w.tile_begin = tiles;
+                    w.has_sponge = m->has_sponge;
+                    w.src_on = m->src_on && m->n < (int)m->amp.size();
+                    w.sx = m->sx;
+                    w.sz = m->sz;
+                    w.src_amp = w.src_on ? m->amp[m->n] : 0.f;
+                    tiles += w.tiles_x * ((m->nz + v.tz - 1) / v.tz);
+                    in.push_back(s0);
+                    ++n;
+                }
+                if (n == 0)
+                    continue;
+                p.nshots = n;
+                if (b->tun.tile == 3)
+                    wide2d_kernel<64, 16><<<tiles, v.threads, 0, b->stream>>>(p);
+                else
+                    wide2d_kernel<64, 32><<<tiles, v.threads, 0, b->stream>>>(p);
+                ++g_launches;
+                FD_CUDA(cudaGetLastError(), "wide batch launch");
+                for (int s : in) {
+                    fd_model *m = b->models[s];
+                    m->cur ^= 1;
+                    pending[s] = (m->nrec > 0 && m->traces && m->n < m->trace_rows) ? m->n : -1;
+                    ++m->n;
+                    ++done[s];
+                }
+            }
+        }
+    }
+    for (size_t s = 0; s < ns; ++s) {
+        fd_model *m = b->models[s];
+        if (pending[s] >= 0) {
+            FD_CUDA(launch_gather(m->buf[m->cur], m->d_rec, m->nrec, m->traces + (size_t)pending[s] * m->nrec,
+                                  b->stream),
+                    "receiver gather");
+            ++g_launches;
+        }
+        m->pending_row = -1;
+    }
+    FD_CUDA(cudaStreamSynchronize(b->stream), "batch run");
+    int err = 0;
+    FD_CUDA(cudaMemcpy(&err, b->d_err, sizeof err, cudaMemcpyDeviceToHost), "error word");
+    if (err) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        return fail(FD_ETIMEOUT, "a wide batch launch gave up on its TMA wait (device code %d)", err);
+    }
+    return FD_OK;
+}
+
 extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each)
 {
     NvtxRange nvtx_range("fd_batch_step");
@@ -670,6 +900,8 @@ extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_ea
     // the models' own streams must be idle before the batch uses their buffers
     for (fd_model *m : b->models)
         FD_CUDA(cudaStreamSynchronize(m->stream), "model stream");
+    if (get_variant(b->tun.tile).wide)
+        return run_wide(b, target);
     for (size_t s = 0; s < ns; ++s) {
         fd_model *m = b->models[s];
         ShotDesc &d = b->shots[s];
@@ -773,9 +1005,11 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
     cudaEvent_t e0, e1;
     FD_CUDA(cudaEventCreate(&e0), "event");
     FD_CUDA(cudaEventCreate(&e1), "event");
-    for (int tile = 0; tile < 3; ++tile)
+    for (int tile = 0; tile < 5; ++tile)
         for (int g : groups)
             for (int cps : {0, 2}) {
+                if (tile >= 3 && cps)
+                    continue;   // the wide schedule has no resident grid to size
                 fd_batch_tuning t{tile, trial_steps, cps, g};
                 fd_status st = fd_batch_set_tuning(b, &t);
                 if (!st)

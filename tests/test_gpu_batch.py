@@ -63,6 +63,8 @@ def assert_same(a, b):
     dict(tile=1, steps_per_launch=37, ctas_per_sm=0, group_mb=0),
     dict(tile=2, steps_per_launch=50, ctas_per_sm=1, group_mb=1),
     dict(tile=0, steps_per_launch=7, ctas_per_sm=2, group_mb=1),
+    dict(tile=3, steps_per_launch=2000, ctas_per_sm=0, group_mb=0),
+    dict(tile=4, steps_per_launch=2000, ctas_per_sm=0, group_mb=1),
 ])
 def test_batch_equals_solo_bitwise(fdlib, tuning):
     shots = small_shots()
@@ -70,12 +72,21 @@ def test_batch_equals_solo_bitwise(fdlib, tuning):
     assert_same(batched(fdlib, shots, nts, tuning), solo(fdlib, shots, nts))
 
 
-def test_batch_uneven_step_counts(fdlib):
+@pytest.mark.parametrize("tile", [0, 3])
+def test_batch_uneven_step_counts(fdlib, tile):
     shots = small_shots(n=4, nt=90, seed=51)
     nts = [90, 17, 0, 64]
     ref = solo(fdlib, shots, nts)
-    got = batched(fdlib, shots, nts, dict(tile=0, steps_per_launch=25, ctas_per_sm=0, group_mb=0))
+    got = batched(fdlib, shots, nts, dict(tile=tile, steps_per_launch=25, ctas_per_sm=0, group_mb=0))
     assert_same(got, ref)
+
+
+def test_wide_schedule_splits_many_shots_over_launches(fdlib):
+    """More shots than one wide launch carries (64): every shot still bitwise equal to its solo run."""
+    shots = small_shots(n=70, nt=12, seed=55)
+    nts = [12 - (i % 3) for i in range(70)]
+    assert_same(batched(fdlib, shots, nts, dict(tile=3, steps_per_launch=1, ctas_per_sm=0, group_mb=0)),
+                solo(fdlib, shots, nts))
 
 
 def test_batch_matches_oracle(fdlib, oracle):
@@ -87,13 +98,14 @@ def test_batch_matches_oracle(fdlib, oracle):
         assert pl.rel_l2(P, Pr) <= 1e-4 and pl.rel_l2(Pold, Poldr) <= 1e-4 and pl.rel_l2(tr, trr) <= 1e-4
 
 
-def test_batch_step_continues_a_run(fdlib):
+@pytest.mark.parametrize("tile", [1, 3])
+def test_batch_step_continues_a_run(fdlib, tile):
     """Two batch calls of 30 + 45 steps equal one solo run of 75."""
     shots = small_shots(n=3, nt=75, seed=53)
     ref = solo(fdlib, shots, [75, 75, 75])
     models = [fdlib.Model.from_shot(s) for s in shots]
     with fdlib.Batch(models) as b:
-        b.set_tuning(tile=1, steps_per_launch=16, ctas_per_sm=0, group_mb=0)
+        b.set_tuning(tile=tile, steps_per_launch=16, ctas_per_sm=0, group_mb=0)
         for m in models:
             fdlib.fd_reset(m.handle)
             fdlib.fd_set_trace_buffer(m.handle, None, 75)
@@ -109,7 +121,7 @@ def test_autotune_picks_a_valid_tuning(fdlib):
     models = [fdlib.Model.from_shot(s) for s in shots]
     with fdlib.Batch(models) as b:
         best = b.autotune(trial_steps=10)
-        assert best["tile"] in (0, 1, 2) and best["steps_per_launch"] == 2000
+        assert best["tile"] in (0, 1, 2, 3, 4) and best["steps_per_launch"] == 2000
         assert b.tuning() == best
         b.run_shots([60] * 4)
         got = [(m.wavefield(with_old=True), m.traces(60)) for m in models]
