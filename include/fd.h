@@ -343,7 +343,8 @@ typedef struct fd_batch_tuning {
                               0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 tiles; or one ordinary
                               launch per time step over all of a group's shots (tensor maps
                               in the launch parameters, up to 64 shots a launch) with
-                              3 = 64 x 16, 4 = 64 x 32 tiles                                */
+                              3 = 64 x 16, 4 = 64 x 32 tiles, or 5 / 6 / 7 = 64 x 16 tiles
+                              in columns of 4 / 8 / 16 per CTA (double-buffered loads)       */
     int steps_per_launch;  /* time steps per persistent launch, >= 1 (persistent only)      */
     int ctas_per_sm;       /* resident CTAs per SM, 0 = as many as fit (persistent only)    */
     int group_mb;          /* L2 budget per shot group in MB, 0 = all shots in one group;

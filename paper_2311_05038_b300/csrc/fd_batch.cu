@@ -397,17 +397,21 @@ struct WideParams {
     int *err;
 };
 
-template <int TX, int TZ>
+// A CTA owns a column of up to ZT tiles stacked along z in one shot and walks
+// down it through a two-stage TMA ring: the load of tile i + 1 is in flight
+// while tile i is computed.  ZT = 1 is one tile per CTA.
+template <int TX, int TZ, int ZT>
 __global__ void __launch_bounds__(TX / 4 * TZ) wide2d_kernel(const __grid_constant__ WideParams prm)
 {
     constexpr int QX = TX / 4;
     constexpr int HX = TX + 8;
     constexpr int HZ = TZ + 8;
+    constexpr int NS = ZT > 1 ? 2 : 1;
     constexpr uint32_t BYTES = (HX * HZ + 2 * TX * TZ) * 4;
-    __shared__ __align__(128) float sP[HX * HZ];
-    __shared__ __align__(128) float sO[TX * TZ];
-    __shared__ __align__(128) float sW[TX * TZ];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(128) float sP[NS][HX * HZ];
+    __shared__ __align__(128) float sO[NS][TX * TZ];
+    __shared__ __align__(128) float sW[NS][TX * TZ];
+    __shared__ __align__(8) uint64_t bar[NS];
     __shared__ int s_abort;
 
     // the shot of this CTA: the last s with shot[s].tile_begin <= blockIdx.x
@@ -421,54 +425,76 @@ __global__ void __launch_bounds__(TX / 4 * TZ) wide2d_kernel(const __grid_consta
     }
     const int s = lo;
     const WideShot &sh = prm.shot[s];
-    const int t = blockIdx.x - sh.tile_begin;
-    const int x0 = (t % sh.tiles_x) * TX;
-    const int z0 = (t / sh.tiles_x) * TZ;
+    const int c = blockIdx.x - sh.tile_begin;          // CTA within the shot
+    const int tiles_z = (sh.nz + TZ - 1) / TZ;
+    const int x0 = (c % sh.tiles_x) * TX;
+    const int tz0 = (c / sh.tiles_x) * ZT;              // first tile row of this column
+    const int nt = min(ZT, tiles_z - tz0);
     const int tid = threadIdx.x;
 
+    auto issue = [&](int i) {
+        const int st = i % NS;
+        const int z0 = (tz0 + i) * TZ;
+        mbar_arrive_expect_tx(&bar[st], BYTES);
+        tma_load_2d(sP[st], &prm.halo[s], &bar[st], x0 - 4, z0 - 4);
+        tma_load_2d(sO[st], &prm.tile[s], &bar[st], x0, z0);
+        tma_load_2d(sW[st], &prm.wmap[s], &bar[st], x0, z0);
+    };
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        for (int st = 0; st < NS; ++st)
+            mbar_init(&bar[st], 1);
         s_abort = 0;
         fence_barrier_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, BYTES);
-        tma_load_2d(sP, &prm.halo[s], &bar, x0 - 4, z0 - 4);
-        tma_load_2d(sO, &prm.tile[s], &bar, x0, z0);
-        tma_load_2d(sW, &prm.wmap[s], &bar, x0, z0);
-    }
+    if (tid == 0)
+        for (int i = 0; i < min(NS, nt); ++i)
+            issue(i);
     // receivers of this shot's previous step, spread over the shot's CTAs
     if (sh.trace_prev) {
-        const int ntiles = sh.tiles_x * ((sh.nz + TZ - 1) / TZ);
-        for (int r = t * blockDim.x + tid; r < sh.nrec; r += ntiles * blockDim.x)
+        const int ncta = sh.tiles_x * ((tiles_z + ZT - 1) / ZT);
+        for (int r = c * blockDim.x + tid; r < sh.nrec; r += ncta * blockDim.x)
             sh.trace_prev[r] = sh.P[sh.rec_idx[r]];
     }
 
     const int tx = tid % QX;
     const int tz = tid / QX;
     const int x = x0 + 4 * tx;
-    const int z = z0 + tz;
     float axv[4] = {0.f, 0.f, 0.f, 0.f};
-    float azv = 0.f;
     if (sh.has_sponge) {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             axv[e] = x + e < sh.px ? sh.ax[x + e] : 0.f;
-        azv = z < sh.nz ? sh.az[z] : 0.f;
     }
-    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
-    if (!ok) {
-        if (tid == 0)
-            raise_error(prm.err, &s_abort, kDevErrTimeout);
-        return;
+    for (int i = 0; i < nt; ++i) {
+        const int st = i % NS;
+        const int z = (tz0 + i) * TZ + tz;
+        const float azv = sh.has_sponge && z < sh.nz ? sh.az[z] : 0.f;
+        const bool ok = __syncthreads_and(mbar_wait(&bar[st], (i / NS) & 1, &s_abort));
+        if (!ok) {
+            if (tid == 0) {
+                raise_error(prm.err, &s_abort, kDevErrTimeout);
+                // the other stage's copy may still be in flight: wait for it (bounded)
+                int never = 0;
+                if (NS > 1 && i + 1 < nt)
+                    mbar_wait(&bar[(i + 1) % NS], ((i + 1) / NS) & 1, &never, kWaitLimitCycles / 8);
+            }
+            return;
+        }
+        float2 r[2], lp[2];
+        tile2d_update<TX>(sP[st], sO[st], sW[st], tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
+        if (sh.src_on && z == sh.sz && (unsigned)(sh.sx - x) < 4u)
+            add_source4(r, sh.sx - x, sh.src_amp);
+        if (z < sh.nz && x < sh.nx)
+            store4(sh.out + (size_t)z * sh.px + x, r, sh.nx - x);
+        if (NS > 1 && i + NS < nt) {
+            __syncthreads();   // every thread has read stage st
+            if (tid == 0) {
+                fence_proxy_async_shared();
+                issue(i + NS);
+            }
+        }
     }
-    float2 r[2], lp[2];
-    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
-    if (sh.src_on && z == sh.sz && (unsigned)(sh.sx - x) < 4u)
-        add_source4(r, sh.sx - x, sh.src_amp);
-    if (z < sh.nz && x < sh.nx)
-        store4(sh.out + (size_t)z * sh.px + x, r, sh.nx - x);
 }
 
 // Compiled tile variants: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16.
@@ -479,6 +505,7 @@ struct Variant {
     int threads;
     size_t smem;
     bool wide = false;   // one launch per time step (wide2d_kernel) instead of the persistent kernel
+    int zt = 1;          // wide: tiles stacked along z per CTA
 };
 
 template <int TX, int TZ>
@@ -491,14 +518,17 @@ static Variant variant()
     return Variant{TX, TZ, (const void *)batch2d_kernel<TX, TZ, kBatchStages>, TX / 4 * TZ + 32, smem};
 }
 
-template <int TX, int TZ>
+template <int TX, int TZ, int ZT>
 static Variant wide_variant()
 {
-    return Variant{TX, TZ, (const void *)wide2d_kernel<TX, TZ>, TX / 4 * TZ, 0, true};
+    Variant v{TX, TZ, (const void *)wide2d_kernel<TX, TZ, ZT>, TX / 4 * TZ, 0, true};
+    v.zt = ZT;
+    return v;
 }
 
 // Tile variants: 0 = 64 x 16, 1 = 64 x 32, 2 = 128 x 16 (persistent kernel);
-// 3 = 64 x 16, 4 = 64 x 32 (one launch per time step).
+// 3 = 64 x 16, 4 = 64 x 32, 5 / 6 / 7 = 64 x 16 with 4 / 8 / 16 tiles stacked
+// along z per CTA (one launch per time step).
 static Variant get_variant(int tile)
 {
     switch (tile) {
@@ -507,9 +537,15 @@ static Variant get_variant(int tile)
     case 2:
         return variant<128, 16>();
     case 3:
-        return wide_variant<64, 16>();
+        return wide_variant<64, 16, 1>();
     case 4:
-        return wide_variant<64, 32>();
+        return wide_variant<64, 32, 1>();
+    case 5:
+        return wide_variant<64, 16, 4>();
+    case 6:
+        return wide_variant<64, 16, 8>();
+    case 7:
+        return wide_variant<64, 16, 16>();
     default:
         return variant<64, 16>();
     }
@@ -715,7 +751,7 @@ extern "C" fd_status fd_batch_set_tuning(fd_batch *b, const fd_batch_tuning *t)
 {
     if (!b || !t)
         return fail(FD_EINVAL, "fd_batch_set_tuning: NULL argument");
-    if (t->tile < 0 || t->tile > 4 || t->steps_per_launch < 1 || t->ctas_per_sm < 0 || t->group_mb < 0)
+    if (t->tile < 0 || t->tile > 7 || t->steps_per_launch < 1 || t->ctas_per_sm < 0 || t->group_mb < 0)
         return fail(FD_EINVAL, "fd_batch_set_tuning: value out of range");
     const bool same = t->tile == b->tun.tile && t->ctas_per_sm == b->tun.ctas_per_sm && t->group_mb == b->tun.group_mb;
     b->tun = *t;
@@ -826,23 +862,36 @@ static fd_status run_wide(fd_batch *b, const std::vector<int> &target)
                     w.nz = m->nz;
                     w.px = m->px;
                     w.tiles_x = (m->nx + v.tx - 1) / v.tx;
-                    w.tile_begin = tiles;
+                    w.tile_begin = tiles;   // first CTA of the shot
                     w.has_sponge = m->has_sponge;
                     w.src_on = m->src_on && m->n < (int)m->amp.size();
                     w.sx = m->sx;
                     w.sz = m->sz;
                     w.src_amp = w.src_on ? m->amp[m->n] : 0.f;
-                    tiles += w.tiles_x * ((m->nz + v.tz - 1) / v.tz);
+                    tiles += w.tiles_x * (((m->nz + v.tz - 1) / v.tz + v.zt - 1) / v.zt);
                     in.push_back(s0);
                     ++n;
                 }
                 if (n == 0)
                     continue;
                 p.nshots = n;
-                if (b->tun.tile == 3)
-                    wide2d_kernel<64, 16><<<tiles, v.threads, 0, b->stream>>>(p);
-                else
-                    wide2d_kernel<64, 32><<<tiles, v.threads, 0, b->stream>>>(p);
+                switch (b->tun.tile) {
+                case 3:
+                    wide2d_kernel<64, 16, 1><<<tiles, v.threads, 0, b->stream>>>(p);
+                    break;
+                case 4:
+                    wide2d_kernel<64, 32, 1><<<tiles, v.threads, 0, b->stream>>>(p);
+                    break;
+                case 5:
+                    wide2d_kernel<64, 16, 4><<<tiles, v.threads, 0, b->stream>>>(p);
+                    break;
+                case 6:
+                    wide2d_kernel<64, 16, 8><<<tiles, v.threads, 0, b->stream>>>(p);
+                    break;
+                default:
+                    wide2d_kernel<64, 16, 16><<<tiles, v.threads, 0, b->stream>>>(p);
+                    break;
+                }
                 ++g_launches;
                 FD_CUDA(cudaGetLastError(), "wide batch launch");
                 for (int s : in) {
@@ -1005,7 +1054,7 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
     cudaEvent_t e0, e1;
     FD_CUDA(cudaEventCreate(&e0), "event");
     FD_CUDA(cudaEventCreate(&e1), "event");
-    for (int tile = 0; tile < 5; ++tile)
+    for (int tile = 0; tile < 8; ++tile)
         for (int g : groups)
             for (int cps : {0, 2}) {
                 if (tile >= 3 && cps)
