@@ -337,6 +337,66 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
     }
 
 
+def measure_batched_3d(nshots=24, nt=300, seed=6):
+    """Uneven 3D shots (cubes 128..256 of the serving mix, layered + random velocity,
+    sponge 20) served three ways: one shot at a time on one stream, one at a time
+    on each of 8 streams at once, and all in one batch (one launch per time step
+    over every model).  Results are compared bitwise."""
+    import torch
+    from paper_2311_05038_b300 import fd
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(np.array([128, 160, 192, 224, 256]), nshots)
+    vels = {int(n): wl.serving_3d_velocity(int(n), 5000 + int(n)) for n in set(sizes.tolist())}
+    shots = [wl.serving_3d_shot(i, int(n), nt, vel=vels[int(n)]) for i, n in enumerate(sizes)]
+    updates = sum(s.npoints for s in shots) * nt
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    models = [fd.Model.from_shot(s) for s in shots]
+
+    def plain():
+        for m in models:
+            m.run_shot(nt)
+        for m in models:
+            fd.fd_synchronize(m.handle)
+
+    t_plain = timed(plain)
+    ref = [m.traces(nt).copy() for m in models]
+    handles = [fd.fd_stream_create(0)[0] for _ in range(8)]
+    smodels = [fd.Model.from_shot(s, stream=handles[i % 8]) for i, s in enumerate(shots)]
+
+    def streams():
+        for m in smodels:
+            m.run_shot(nt)
+        for m in smodels:
+            fd.fd_synchronize(m.handle)
+
+    t_streams = timed(streams)
+    same_streams = all(np.array_equal(m.traces(nt), r) for m, r in zip(smodels, ref))
+    for m in smodels:
+        m.close()
+    for h in handles:
+        fd.fd_stream_destroy(h)
+    batch = fd.Batch(models)
+    t_batch = timed(lambda: batch.run_shots([nt] * nshots))
+    same = all(np.array_equal(m.traces(nt), r) for m, r in zip(models, ref))
+    batch.close()
+    for m in models:
+        m.close()
+    arm = lambda t: {"s": t, "shots_per_s": nshots / t, "gupd": updates / t / 1e9}
+    return {"workload": f"{nshots} 3D shots, cubes {int(sizes.min())}..{int(sizes.max())}, {nt} steps, sponge 20",
+            "plain": arm(t_plain), "plain_streams": dict(arm(t_streams), streams=8,
+                                                         results_identical=bool(same_streams)),
+            "batched": arm(t_batch), "speedup": t_plain / t_batch, "speedup_vs_streams": t_streams / t_batch,
+            "results_identical": bool(same)}
+
+
 # ------------------------------------------------------------------------ serving 3D
 
 def measure_serving(nshots=500, closed_shots=100, max_active=4, load=0.8, budget_gb=150):
@@ -662,10 +722,11 @@ def run_b300(args, dist, rank, local, world):
                "sample": f"{args.n}^3 layered grid with sponge, source and receivers, {steps} of "
                          f"{args.nt} time steps, FP64 oracle, {el:.1f} s"}
 
-    batched = None
+    batched = batched3 = None
     if rank == 0 and not args.skip_batched:
         torch.cuda.empty_cache()
         batched = measure_batched(args.shots, args.batch_nt)
+        batched3 = measure_batched_3d()
     adj = None
     if rank == 0 and not args.skip_adjoint:
         torch.cuda.empty_cache()
@@ -696,6 +757,7 @@ def run_b300(args, dist, rank, local, world):
             "clocks": clocks.summary(),
             "gpu_launches": int(launches),
             "batched_2d": batched,
+            "batched_3d": batched3,
             "serving_3d": served,
             "adjoint_3d": adj,
             "unfused_3d": unfused,

@@ -351,8 +351,12 @@ typedef struct fd_batch_tuning {
                               the groups run one after another                              */
 } fd_batch_tuning;
 
-/* Build a batch over nmodels 2D models on the same device (FD_EINVAL for 3D
- * models, NULL entries or a repeated model). */
+/* Build a batch over nmodels models on the same device, all 2D or all 3D
+ * (FD_EINVAL for a mix, NULL entries or a repeated model).  2D batches run the
+ * schedule of their tuning.  3D batches run one launch per time step over up to
+ * 48 models that still have steps to go, each CTA stepping its own model with
+ * the single-shot 3D kernel (maps and parameters in the launch); their tuning
+ * is not used, and fd_batch_autotune leaves it unchanged. */
 fd_status fd_batch_create(fd_model *const *models, int nmodels, fd_batch **out);
 fd_status fd_batch_destroy(fd_batch *b);
 /* Set / read the tuning (validated; FD_EINVAL for out-of-range values). */

@@ -665,6 +665,39 @@ static fd_status flush_pending(fd_model *m)
     return FD_OK;
 }
 
+void fdk::fill_step_params(fd_model *m, StepParams &p)
+{
+    float w4[4];
+    fd_stencil_weights(w4);
+    p = StepParams{};
+    p.stall_stage = m->stall_stage;
+    p.c1 = w4[0];
+    p.c2 = w4[1];
+    p.c3 = w4[2];
+    p.c4 = w4[3];
+    p.ax = m->ax;
+    p.ay = m->ay;
+    p.az = m->az;
+    p.nx = m->nx;
+    p.ny = m->ny;
+    p.nz = m->nz;
+    p.px = m->px;
+    p.bz = m->bz;
+    p.has_sponge = m->has_sponge;
+    p.sx = m->sx;
+    p.sy = m->sy;
+    p.sz = m->sz;
+    p.rec_idx = m->d_rec;
+    p.nrec = m->nrec;
+    p.err = m->d_err;
+    const int c = m->cur;
+    p.out = m->buf[c ^ 1];
+    p.P = m->buf[c];
+    p.src_on = m->src_on && m->n < (int)m->amp.size();
+    p.src_amp = p.src_on ? m->amp[m->n] : 0.f;
+    p.trace_prev = m->pending_row >= 0 ? m->traces + (size_t)m->pending_row * m->nrec : nullptr;
+}
+
 // Two fused steps: levels n+1, n+2 into the spare buffers, which then take the
 // places of buf[] (with their maps).  The launch gathers the receiver rows still
 // owed for its two input levels (pending_old from Pold, m->pending_row from P).
@@ -752,38 +785,12 @@ static fd_status step_n(fd_model *m, int nsteps, float *lp, const float *img_lp 
         return st;
     nsteps -= s0;
     StepParams p{};
-    p.stall_stage = m->stall_stage;
-    p.lp_out = lp;
-    p.img_lp = img_lp;
-    p.img_grad = img_grad;
-    float w4[4];
-    fd_stencil_weights(w4);
-    p.c1 = w4[0];
-    p.c2 = w4[1];
-    p.c3 = w4[2];
-    p.c4 = w4[3];
-    p.ax = m->ax;
-    p.ay = m->ay;
-    p.az = m->az;
-    p.nx = m->nx;
-    p.ny = m->ny;
-    p.nz = m->nz;
-    p.px = m->px;
-    p.bz = m->bz;
-    p.has_sponge = m->has_sponge;
-    p.sx = m->sx;
-    p.sy = m->sy;
-    p.sz = m->sz;
-    p.rec_idx = m->d_rec;
-    p.nrec = m->nrec;
-    p.err = m->d_err;
     for (int s = 0; s < nsteps; ++s) {
         const int c = m->cur;
-        p.out = m->buf[c ^ 1];
-        p.P = m->buf[c];
-        p.src_on = m->src_on && m->n < (int)m->amp.size();
-        p.src_amp = p.src_on ? m->amp[m->n] : 0.f;
-        p.trace_prev = m->pending_row >= 0 ? m->traces + (size_t)m->pending_row * m->nrec : nullptr;
+        fill_step_params(m, p);
+        p.lp_out = lp;
+        p.img_lp = img_lp;
+        p.img_grad = img_grad;
         cudaError_t e = m->d.ndim == 3
                             ? launch_step3d(m->halo_map[c], m->tile_map[c ^ 1], m->w_map, p, m->nchunks, m->stream)
                             : launch_step2d(m->halo_map[c], m->tile_map[c ^ 1], m->w_map, p, m->stream);

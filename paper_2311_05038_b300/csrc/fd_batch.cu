@@ -575,6 +575,7 @@ struct fd_batch {
     std::vector<ShotDesc> shots;   // host copy (tensor maps, pointers)
     std::vector<int> group_shot;   // first shot of each group, then the shot count
     WideParams wide{};             // parameter block of the wide schedule's launches
+    Wide3Params wide3{};           // ... and of the batched 3D schedule's
     int stall_item = -1;           // fd_batch_set_fault
 };
 
@@ -702,8 +703,8 @@ extern "C" fd_status fd_batch_create(fd_model *const *models, int nmodels, fd_ba
     for (int i = 0; i < nmodels; ++i) {
         if (!models[i])
             return fail(FD_EINVAL, "fd_batch_create: model %d is NULL", i);
-        if (models[i]->d.ndim != 2)
-            return fail(FD_EINVAL, "fd_batch_create: model %d is not 2D", i);
+        if (models[i]->d.ndim != models[0]->d.ndim)
+            return fail(FD_EINVAL, "fd_batch_create: model %d mixes 2D and 3D models", i);
         if (models[i]->device != models[0]->device)
             return fail(FD_EINVAL, "fd_batch_create: models on different devices");
         for (int j = 0; j < i; ++j)
@@ -924,6 +925,93 @@ static fd_status run_wide(fd_batch *b, const std::vector<int> &target)
     return FD_OK;
 }
 
+// 3D batches: one launch per time step over up to kWide3Max models that still
+// have steps to go, each CTA stepping its own model with the single-shot 3D
+// kernel's body (maps and parameters from the launch).  The launch gathers each
+// model's owed receiver row; the rows owed at the end are gathered per model.
+static fd_status run_wide3d(fd_batch *b, const std::vector<int> &target)
+{
+    FD_CUDA(step3d_prepare(), "kernel attributes");
+    Wide3Params &w = b->wide3;
+    const size_t ns = b->models.size();
+    std::vector<int> done(ns, 0);
+    // z chunks for the launch as a whole: about six waves of CTAs over all models,
+    // each CTA marching at least 32 planes (a model alone would cut small grids
+    // into short chunks to fill the GPU, paying their halo planes again and again)
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const long long slots = (long long)sms * step3d_blocks_per_sm();
+    long long col_planes = 0;
+    for (const fd_model *m : b->models)
+        col_planes += (long long)((m->nx + kTX3 - 1) / kTX3) * ((m->ny + kTY3 - 1) / kTY3) * m->nz;
+    const long long bz_t = std::max(32LL, col_planes / (6 * slots));
+    std::vector<int> nch(ns), bzs(ns);
+    for (size_t s = 0; s < ns; ++s) {
+        const int nz = b->models[s]->nz;
+        nch[s] = (int)((nz + std::min<long long>(bz_t, nz) - 1) / std::min<long long>(bz_t, nz));
+        bzs[s] = (nz + nch[s] - 1) / nch[s];
+    }
+    int kmax = 0;
+    for (int t : target)
+        kmax = std::max(kmax, t);
+    for (int k = 0; k < kmax; ++k) {
+        for (size_t s0 = 0; s0 < ns;) {
+            int n = 0, ctas = 0;
+            std::vector<size_t> in;
+            for (; s0 < ns && n < kWide3Max; ++s0) {
+                if (done[s0] >= target[s0])
+                    continue;
+                fd_model *m = b->models[s0];
+                const int c = m->cur;
+                w.tmP[n] = m->halo_map[c];
+                w.tmOld[n] = m->tile_map[c ^ 1];
+                w.tmW[n] = m->w_map;
+                fill_step_params(m, w.prm[n]);
+                w.prm[n].stall_stage = -1;
+                w.prm[n].bz = bzs[s0];
+                w.tiles[n] = ((m->nx + kTX3 - 1) / kTX3) * ((m->ny + kTY3 - 1) / kTY3);
+                w.cta_begin[n] = ctas;
+                ctas += w.tiles[n] * nch[s0];
+                in.push_back(s0);
+                ++n;
+            }
+            if (n == 0)
+                continue;
+            w.nmodels = n;
+            w.cta_begin[n] = ctas;
+            FD_CUDA(launch_wide3d(w, b->stream), "batched 3D launch");
+            ++g_launches;
+            for (size_t s : in) {
+                fd_model *m = b->models[s];
+                m->cur ^= 1;
+                m->pending_row = (m->nrec > 0 && m->traces && m->n < m->trace_rows) ? m->n : -1;
+                ++m->n;
+                ++done[s];
+            }
+        }
+    }
+    for (fd_model *m : b->models) {
+        if (m->pending_row >= 0) {
+            FD_CUDA(launch_gather(m->buf[m->cur], m->d_rec, m->nrec, m->traces + (size_t)m->pending_row * m->nrec,
+                                  b->stream),
+                    "receiver gather");
+            ++g_launches;
+        }
+        m->pending_row = -1;
+    }
+    FD_CUDA(cudaStreamSynchronize(b->stream), "batch run");
+    // the step kernels report a bounded wait that gave up in each model's error word
+    for (fd_model *m : b->models) {
+        int err = 0;
+        FD_CUDA(cudaMemcpy(&err, m->d_err, sizeof err, cudaMemcpyDeviceToHost), "error word");
+        if (err) {
+            cudaMemset(m->d_err, 0, sizeof(int));
+            return fail(FD_ETIMEOUT, "a batched 3D step gave up on a bounded wait (device code %d)", err);
+        }
+    }
+    return FD_OK;
+}
+
 extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each)
 {
     NvtxRange nvtx_range("fd_batch_step");
@@ -940,6 +1028,11 @@ extern "C" fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_ea
         if (target[s] < 0)
             return fail(FD_EINVAL, "negative step count for shot %zu", s);
         tmax = std::max(tmax, target[s]);
+    }
+    if (b->models[0]->d.ndim == 3) {
+        for (fd_model *m : b->models)
+            FD_CUDA(cudaStreamSynchronize(m->stream), "model stream");
+        return run_wide3d(b, target);
     }
     if (!b->built) {
         fd_status st = build_tables(b);
@@ -1033,6 +1126,11 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
     NvtxRange nvtx_range("fd_batch_autotune");
     if (!b || trial_steps < 1)
         return fail(FD_EINVAL, "fd_batch_autotune: bad arguments");
+    if (b->models[0]->d.ndim == 3) {   // a 3D batch has one schedule: nothing to tune
+        if (best)
+            *best = b->tun;
+        return FD_OK;
+    }
     const std::string sig = batch_signature(b) + "/" + std::to_string(trial_steps);
     auto hit = g_tuning_cache.find(sig);
     if (hit != g_tuning_cache.end()) {

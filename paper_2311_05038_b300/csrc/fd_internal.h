@@ -105,6 +105,24 @@ cudaError_t step3d_t2_prepare();
 cudaError_t launch_step3d_t2(const CUtensorMap &tmP1, const CUtensorMap &tmP0, const CUtensorMap &tmW,
                              const T2Params &p, int nchunks, cudaStream_t s);
 
+// One time step of up to kWide3Max 3D models in one launch (the batched 3D
+// schedule): per model its three tensor maps and step parameters, its first CTA
+// (cta_begin[nmodels] = total CTAs) and its CTAs per z chunk.
+constexpr int kWide3Max = 48;
+struct Wide3Params {
+    CUtensorMap tmP[kWide3Max];
+    CUtensorMap tmOld[kWide3Max];
+    CUtensorMap tmW[kWide3Max];
+    StepParams prm[kWide3Max];
+    int cta_begin[kWide3Max + 1];
+    int tiles[kWide3Max];
+    int nmodels;
+};
+cudaError_t launch_wide3d(const Wide3Params &w, cudaStream_t s);
+// The step parameters of one plain time step of model m at its current state
+// (levels, step counter, source amplitude, owed receiver row).
+void fill_step_params(fd_model *m, StepParams &p);
+
 size_t step3d_smem_bytes();
 cudaError_t step3d_prepare();
 int step3d_blocks_per_sm();

@@ -18,14 +18,14 @@
 
 namespace fdk {
 
-// Gather of the previous step's receiver row, spread over every thread of the grid.
-__device__ __forceinline__ void gather_prev_row(const StepParams &prm)
+// Gather of the previous step's receiver row, spread over every thread of the
+// ncta CTAs that step the model (this CTA is number cta of them).
+__device__ __forceinline__ void gather_prev_row(const StepParams &prm, int64_t cta, int64_t ncta)
 {
     if (!prm.trace_prev)
         return;
-    const int64_t nthr = (int64_t)gridDim.x * gridDim.y * blockDim.x;
-    for (int64_t r = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-         r < prm.nrec; r += nthr)
+    const int64_t nthr = ncta * blockDim.x;
+    for (int64_t r = cta * blockDim.x + threadIdx.x; r < prm.nrec; r += nthr)
         prm.trace_prev[r] = prm.P[prm.rec_idx[r]];
 }
 
@@ -57,10 +57,15 @@ __device__ __forceinline__ void gather_prev_row(const StepParams &prm)
 // fd_pzz): they stream P through the same ring and write only
 // sum_k c_k (P[+k] + P[-k] - 2P) along x, y or z to prm.out, with no Pold or w
 // loads.
+//
+// The body is a device function of the CTA's column bx (in x-fastest order) and
+// z chunk by, so that one launch can also step several models (the batched 3D
+// schedule, each CTA with its own model's maps and parameters); step3d_kernel
+// runs it for one model with (bx, by) = blockIdx.  The tensor maps must stay in
+// parameter space (references to __grid_constant__ parameters).
 template <int TX, int TY, int SP, int ST, int G, int MODE>
-__global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
-    step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
-                  const __grid_constant__ CUtensorMap tmW, const StepParams prm)
+__device__ __forceinline__ void step3d_body(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
+                                            const StepParams &prm, int bx, int by, int64_t cta, int64_t ncta)
 {
     constexpr int QX = TX / 4;
     constexpr int NT = QX * TY;
@@ -93,9 +98,9 @@ __global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
     __shared__ int s_issuedP, s_issuedT;
 
     const int tiles_x = (prm.nx + TX - 1) / TX;
-    const int x0 = (blockIdx.x % tiles_x) * TX;
-    const int y0 = (blockIdx.x / tiles_x) * TY;
-    const int z0 = blockIdx.y * prm.bz;
+    const int x0 = (bx % tiles_x) * TX;
+    const int y0 = (bx / tiles_x) * TY;
+    const int z0 = by * prm.bz;
     const int z1 = min(prm.nz, z0 + prm.bz);
     const int nb = z1 - z0;
     const int nbh = (nb + 1) >> 1;
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
 
     auto issueP = [&](int k, int slot) {
         if constexpr (MODE == 3) {
-            if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0) {
+            if (k == prm.stall_stage && bx == 0 && by == 0) {
                 // test hook: the stage is counted as issued but never loaded, so this
                 // CTA's bounded waits run out; the drain below skips it
                 atomicAdd(&s_issuedP, 1);
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
         }
     }
 
-    gather_prev_row(prm);
+    gather_prev_row(prm, cta, ncta);
 
     const int tx = tid % QX;
     const int ty = tid / QX;
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
         // after every warp has freed stage k
         for (int k = max(0, s_issuedP - SP); k < s_issuedP; ++k) {
             if constexpr (MODE == 3) {
-                if (k == prm.stall_stage && blockIdx.x == 0 && blockIdx.y == 0)
+                if (k == prm.stall_stage && bx == 0 && by == 0)
                     continue;   // withheld by the test hook: nothing in flight
             }
             mbar_wait(&fullP[k % SP], (k / SP) & 1, &never, kWaitLimitCycles / 8);
@@ -432,6 +437,37 @@ __global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
         for (int t = max(0, s_issuedT - ST); t < s_issuedT; ++t)
             mbar_wait(&fullT[t % ST], (t / ST) & 1, &never, kWaitLimitCycles / 8);
     }
+}
+
+template <int TX, int TY, int SP, int ST, int G, int MODE>
+__global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
+    step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
+                  const __grid_constant__ CUtensorMap tmW, const StepParams prm)
+{
+    step3d_body<TX, TY, SP, ST, G, MODE>(tmP, tmOld, tmW, prm, blockIdx.x, blockIdx.y,
+                                         (int64_t)blockIdx.y * gridDim.x + blockIdx.x,
+                                         (int64_t)gridDim.x * gridDim.y);
+}
+
+// Several 3D models in one launch, one time step each (the batched 3D schedule):
+// a CTA finds its model by a binary search over the models' first CTAs in the
+// launch parameters and runs the step body with that model's tensor maps and
+// parameters, all in parameter space.
+__global__ void __launch_bounds__(kThreads3, kMinBlocks3) wide3d_kernel(const __grid_constant__ Wide3Params w)
+{
+    int lo = 0, hi = w.nmodels - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.cta_begin[mid] <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int m = lo;
+    const int c = blockIdx.x - w.cta_begin[m];
+    const int tiles = w.tiles[m];
+    step3d_body<kTX3, kTY3, kStagesP3, kStagesT3, kGroup3, 0>(w.tmP[m], w.tmOld[m], w.tmW[m], w.prm[m], c % tiles,
+                                                              c / tiles, c, w.cta_begin[m + 1] - w.cta_begin[m]);
 }
 
 // ----------------------------------------------------------------------------- 2D
@@ -471,7 +507,7 @@ __global__ void __launch_bounds__(TX / 4 * TZ)
         tma_load_2d(sO, &tmOld, &bar, x0, z0);
         tma_load_2d(sW, &tmW, &bar, x0, z0);
     }
-    gather_prev_row(prm);
+    gather_prev_row(prm, blockIdx.x, gridDim.x);
 
     const int tx = tid % QX;
     const int tz = tid / QX;
@@ -576,6 +612,8 @@ cudaError_t step3d_prepare()
     const int bytes = (int)step3d_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(FD_STEP3D(0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(wide3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(FD_STEP3D(1), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(FD_STEP3D(2), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -618,6 +656,12 @@ cudaError_t launch_step3d(const CUtensorMap &tmP, const CUtensorMap &tmOld, cons
         FD_STEP3D(3)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
     else
         FD_STEP3D(0)<<<grid, kThreads3, step3d_smem_bytes(), s>>>(tmP, tmOld, tmW, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide3d(const Wide3Params &w, cudaStream_t s)
+{
+    wide3d_kernel<<<w.cta_begin[w.nmodels], kThreads3, step3d_smem_bytes(), s>>>(w);
     return cudaGetLastError();
 }
 

@@ -131,11 +131,11 @@ def test_autotune_picks_a_valid_tuning(fdlib):
     assert_same(got, solo(fdlib, shots, [60] * 4))
 
 
-def test_batch_rejects_3d_models(fdlib):
+def test_batch_rejects_a_mix_of_2d_and_3d_models(fdlib):
     shot = wl.roofline_3d(shape=(16, 16, 16), nt=4, sponge_width=0)
-    with fdlib.Model.from_shot(shot) as m:
+    with fdlib.Model.from_shot(shot) as m, fdlib.Model.from_shot(small_shots(n=1)[0]) as m2:
         with pytest.raises(fdlib.FDError) as e:
-            fdlib.fd_batch_create([m.handle])
+            fdlib.fd_batch_create([m.handle, m2.handle])
         assert e.value.status == fdlib.FD_EINVAL
 
 
