@@ -21,7 +21,7 @@ constexpr int kRadius = 4;
 #define FD_TX3 32
 #endif
 #ifndef FD_TY3
-#define FD_TY3 32
+#define FD_TY3 16
 #endif
 #ifndef FD_STAGESP3
 #define FD_STAGESP3 5
@@ -33,7 +33,7 @@ constexpr int kRadius = 4;
 #define FD_QGROUP3 2
 #endif
 #ifndef FD_MINB3
-#define FD_MINB3 2
+#define FD_MINB3 4
 #endif
 constexpr int kTX3 = FD_TX3;
 constexpr int kTY3 = FD_TY3;

@@ -440,7 +440,7 @@ __device__ __forceinline__ void step3d_body(const CUtensorMap &tmP, const CUtens
 }
 
 template <int TX, int TY, int SP, int ST, int G, int MODE>
-__global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 3 : kMinBlocks3)
+__global__ void __launch_bounds__(TX / 4 * TY, MODE >= 4 ? 768 / (TX / 4 * TY) : kMinBlocks3)
     step3d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
 {
