@@ -397,6 +397,31 @@ def measure_batched_3d(nshots=24, nt=300, seed=6):
             "results_identical": bool(same)}
 
 
+def measure_2d_large(n=8192, nt=200):
+    """One large 2D shot (n x n, GRF-free layered-constant velocity 2000 m/s, sponge
+    20): device Gupd/s of fd_step, 16 algorithmic bytes per update."""
+    import torch
+    from paper_2311_05038_b300 import fd
+    vel = np.full((n, n), 2000.0, np.float32)
+    dt = wl.courant_dt(10.0, 2000.0)
+    rec = np.array([(ix, 0, 32) for ix in range(0, n, 4)], np.int32)
+    shot = wl.Shot(2, (n, n), 10.0, dt, nt, vel, (n // 2, 0, n // 2), wl.ricker(nt, dt, 15.0), rec, sponge_width=20)
+    stream = torch.cuda.Stream()
+    with fd.Model.from_shot(shot, stream=stream) as m:
+        m.run_shot(20)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.run_shot(nt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    peak, _ = measured_hbm_peak()
+    gupd = n * n * nt / t / 1e9
+    return {"workload": f"2D {n}x{n}, {nt} steps, sponge 20", "gupd": gupd, "frac": 16 * gupd / peak}
+
+
 # ------------------------------------------------------------------------ serving 3D
 
 def measure_serving(nshots=500, closed_shots=100, max_active=4, load=0.8, budget_gb=150):
@@ -727,6 +752,7 @@ def run_b300(args, dist, rank, local, world):
         torch.cuda.empty_cache()
         batched = measure_batched(args.shots, args.batch_nt)
         batched3 = measure_batched_3d()
+        batched["single_shot_2d_large"] = measure_2d_large()
     adj = None
     if rank == 0 and not args.skip_adjoint:
         torch.cuda.empty_cache()

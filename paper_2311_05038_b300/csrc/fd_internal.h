@@ -44,9 +44,12 @@ constexpr int kGroup3 = FD_QGROUP3;      // stages per unrolled z-queue rotation
 constexpr int kMinBlocks3 = FD_MINB3;
 constexpr int kThreads3 = kTX3 / 4 * kTY3;
 
-// 2D step: a CTA owns one kTX2 x kTZ2 tile.
+// 2D step: a CTA owns a column of kZT2 tiles of kTX2 x kTZ2 points stacked along
+// z (one tile when the grid would give fewer than kStackMinCtas2 such columns).
 constexpr int kTX2 = 64;
 constexpr int kTZ2 = 16;
+constexpr int kZT2 = 8;
+constexpr int kStackMinCtas2 = 4096;
 constexpr int kThreads2 = kTX2 / 4 * kTZ2;
 
 // Codes a kernel writes into the model's device error word.

@@ -472,10 +472,12 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3) wide3d_kernel(const __
 
 // ----------------------------------------------------------------------------- 2D
 
-// A CTA owns one TX x TZ tile of the [nz][nx] grid.  One TMA transaction brings
-// the haloed P tile and the Pold and w tiles; each thread computes 4
-// consecutive x points of one row.
-template <int TX, int TZ, int MODE>
+// A CTA owns a column of up to ZT tiles of TX x TZ points of the [nz][nx] grid,
+// stacked along z, and walks down it through a two-stage TMA ring: one TMA
+// transaction brings a tile's haloed P box and its Pold and w tiles, and the
+// next tile's transaction is in flight while a tile is computed.  Each thread
+// computes 4 consecutive x points of one row.  ZT = 1 is one tile per CTA.
+template <int TX, int TZ, int ZT, int MODE>
 __global__ void __launch_bounds__(TX / 4 * TZ)
     step2d_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmOld,
                   const __grid_constant__ CUtensorMap tmW, const StepParams prm)
@@ -483,61 +485,84 @@ __global__ void __launch_bounds__(TX / 4 * TZ)
     constexpr int QX = TX / 4;
     constexpr int HX = TX + 8;
     constexpr int HZ = TZ + 8;
+    constexpr int NS = ZT > 1 ? 2 : 1;
     constexpr uint32_t BYTES = (HX * HZ + 2 * TX * TZ) * 4;
-    __shared__ __align__(128) float sP[HX * HZ];
-    __shared__ __align__(128) float sO[TX * TZ];
-    __shared__ __align__(128) float sW[TX * TZ];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(128) float sP[NS][HX * HZ];
+    __shared__ __align__(128) float sO[NS][TX * TZ];
+    __shared__ __align__(128) float sW[NS][TX * TZ];
+    __shared__ __align__(8) uint64_t bar[NS];
     __shared__ int s_abort;
 
     const int tiles_x = (prm.nx + TX - 1) / TX;
+    const int tiles_z = (prm.nz + TZ - 1) / TZ;
     const int x0 = (blockIdx.x % tiles_x) * TX;
-    const int z0 = (blockIdx.x / tiles_x) * TZ;
+    const int tz0 = (blockIdx.x / tiles_x) * ZT;   // first tile row of this column
+    const int nt = min(ZT, tiles_z - tz0);
     const int tid = threadIdx.x;
 
+    auto issue = [&](int i) {
+        const int st = i % NS;
+        const int z0 = (tz0 + i) * TZ;
+        mbar_arrive_expect_tx(&bar[st], BYTES);
+        tma_load_2d(sP[st], &tmP, &bar[st], x0 - 4, z0 - 4);
+        tma_load_2d(sO[st], &tmOld, &bar[st], x0, z0);
+        tma_load_2d(sW[st], &tmW, &bar[st], x0, z0);
+    };
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        for (int st = 0; st < NS; ++st)
+            mbar_init(&bar[st], 1);
         s_abort = 0;
         fence_barrier_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, BYTES);
-        tma_load_2d(sP, &tmP, &bar, x0 - 4, z0 - 4);
-        tma_load_2d(sO, &tmOld, &bar, x0, z0);
-        tma_load_2d(sW, &tmW, &bar, x0, z0);
-    }
+    if (tid == 0)
+        for (int i = 0; i < min(NS, nt); ++i)
+            issue(i);
     gather_prev_row(prm, blockIdx.x, gridDim.x);
 
     const int tx = tid % QX;
     const int tz = tid / QX;
     const int x = x0 + 4 * tx;
-    const int z = z0 + tz;
     float axv[4] = {0.f, 0.f, 0.f, 0.f};
-    float azv = 0.f;
     if (prm.has_sponge) {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             axv[e] = x + e < prm.px ? prm.ax[x + e] : 0.f;
-        azv = z < prm.nz ? prm.az[z] : 0.f;
     }
-    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
-    if (!ok) {
-        if (tid == 0)
-            raise_error(prm.err, &s_abort, kDevErrTimeout);
-        return;
-    }
-    float2 r[2], lp[2];
-    tile2d_update<TX>(sP, sO, sW, tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
-    if (prm.src_on && z == prm.sz && (unsigned)(prm.sx - x) < 4u)
-        add_source4(r, prm.sx - x, prm.src_amp);
-    if (z < prm.nz && x < prm.nx) {
-        store4(prm.out + (size_t)z * prm.px + x, r, prm.nx - x);
-        if constexpr (MODE == 1)
-            store4_dense(prm.lp_out + (size_t)z * prm.nx + x, lp, prm.nx - x, (prm.nx & 3) == 0);
-        if constexpr (MODE == 2)
-            image4_dense(prm.img_grad + (size_t)z * prm.nx + x, prm.img_lp + (size_t)z * prm.nx + x, r,
-                         prm.nx - x, (prm.nx & 3) == 0);
+    for (int i = 0; i < nt; ++i) {
+        const int st = i % NS;
+        const int z = (tz0 + i) * TZ + tz;
+        const float azv = prm.has_sponge && z < prm.nz ? prm.az[z] : 0.f;
+        const bool ok = __syncthreads_and(mbar_wait(&bar[st], (i / NS) & 1, &s_abort));
+        if (!ok) {
+            if (tid == 0) {
+                raise_error(prm.err, &s_abort, kDevErrTimeout);
+                // the other stage's copy may still be in flight: wait for it (bounded)
+                int never = 0;
+                if (NS > 1 && i + 1 < nt)
+                    mbar_wait(&bar[(i + 1) % NS], ((i + 1) / NS) & 1, &never, kWaitLimitCycles / 8);
+            }
+            return;
+        }
+        float2 r[2], lp[2];
+        tile2d_update<TX>(sP[st], sO[st], sW[st], tx, tz, axv, azv, prm.c1, prm.c2, prm.c3, prm.c4, r, lp);
+        if (prm.src_on && z == prm.sz && (unsigned)(prm.sx - x) < 4u)
+            add_source4(r, prm.sx - x, prm.src_amp);
+        if (z < prm.nz && x < prm.nx) {
+            store4(prm.out + (size_t)z * prm.px + x, r, prm.nx - x);
+            if constexpr (MODE == 1)
+                store4_dense(prm.lp_out + (size_t)z * prm.nx + x, lp, prm.nx - x, (prm.nx & 3) == 0);
+            if constexpr (MODE == 2)
+                image4_dense(prm.img_grad + (size_t)z * prm.nx + x, prm.img_lp + (size_t)z * prm.nx + x, r,
+                             prm.nx - x, (prm.nx & 3) == 0);
+        }
+        if (NS > 1 && i + NS < nt) {
+            __syncthreads();   // every thread has read stage st
+            if (tid == 0) {
+                fence_proxy_async_shared();
+                issue(i + NS);
+            }
+        }
     }
 }
 
@@ -665,16 +690,29 @@ cudaError_t launch_wide3d(const Wide3Params &w, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Columns of kZT2 tiles per CTA when the grid has tiles for several waves of
+// them, else one tile per CTA so that small grids still spread over the SMs.
+template <int ZT>
+static void launch_step2d_zt(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
+                             const StepParams &p, int ctas, cudaStream_t s)
+{
+    if (p.lp_out)
+        step2d_kernel<kTX2, kTZ2, ZT, 1><<<ctas, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    else if (p.img_grad)
+        step2d_kernel<kTX2, kTZ2, ZT, 2><<<ctas, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    else
+        step2d_kernel<kTX2, kTZ2, ZT, 0><<<ctas, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+}
+
 cudaError_t launch_step2d(const CUtensorMap &tmP, const CUtensorMap &tmOld, const CUtensorMap &tmW,
                           const StepParams &p, cudaStream_t s)
 {
-    const int tiles = ((p.nx + kTX2 - 1) / kTX2) * ((p.nz + kTZ2 - 1) / kTZ2);
-    if (p.lp_out)
-        step2d_kernel<kTX2, kTZ2, 1><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
-    else if (p.img_grad)
-        step2d_kernel<kTX2, kTZ2, 2><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+    const int tiles_x = (p.nx + kTX2 - 1) / kTX2, tiles_z = (p.nz + kTZ2 - 1) / kTZ2;
+    const long long stacked = (long long)tiles_x * ((tiles_z + kZT2 - 1) / kZT2);
+    if (stacked >= kStackMinCtas2)
+        launch_step2d_zt<kZT2>(tmP, tmOld, tmW, p, (int)stacked, s);
     else
-        step2d_kernel<kTX2, kTZ2, 0><<<tiles, kThreads2, 0, s>>>(tmP, tmOld, tmW, p);
+        launch_step2d_zt<1>(tmP, tmOld, tmW, p, tiles_x * tiles_z, s);
     return cudaGetLastError();
 }
 

@@ -478,3 +478,37 @@ def test_parity_3d_roofline_full_run(fdlib):
     assert max(e_plane, e_row, e_P, e_O, e_T) <= TOL, (e_plane, e_row, e_P, e_O, e_T)
     for got, key in ((nP, "norm_P"), (nO, "norm_Pold"), (nT, "norm_traces")):
         assert abs(got / float(ref[key]) - 1.0) <= TOL, key
+
+
+def test_parity_2d_large_grid_stacked_tiles(fdlib, oracle):
+    """A 2D grid large enough for the step kernel's columns of 8 stacked tiles
+    (8150 x 4100: ragged in x and in the last column's tile count), from a random
+    state with sponge, source and receivers: against the oracle (rel L2 <= 1e-4),
+    and bitwise against the same steps through the wide batch schedule with one
+    tile per CTA (the same per-tile arithmetic)."""
+    shape = (8150, 4100)
+    rng = np.random.default_rng(61)
+    vel = rng.uniform(1500.0, 3000.0, shape).astype(np.float32)
+    dt = wl.courant_dt(10.0, 3000.0)
+    nt = 4
+    rec = np.array([(int(rng.integers(0, 4100)), 0, int(rng.integers(0, 8150))) for _ in range(300)], np.int32)
+    shot = wl.Shot(2, shape, 10.0, dt, nt, vel, (2049, 0, 4001), wl.ricker(nt, dt, 15.0, t0=0.0), rec,
+                   sponge_width=10)
+    P0, Pm1 = wl.random_state(shape, seed=62)
+    out = []
+    for batched in (False, True):
+        with fdlib.Model.from_shot(shot) as m:
+            fdlib.fd_set_trace_buffer(m.handle, None, nt)
+            fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
+            if batched:
+                with fdlib.Batch([m]) as b:
+                    b.set_tuning(tile=3, steps_per_launch=2000, ctas_per_sm=0, group_mb=0)
+                    b.step(nt)
+            else:
+                m.step(nt)
+            out.append((*m.wavefield(with_old=True), m.traces(nt)))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    ref = oracle.run(2, shape, shot.h, dt, vel, sponge_width=10, src=shot.src, wavelet=shot.wavelet,
+                     receivers=rec, P=P0, Pold=Pm1, nsteps=nt)
+    assert max(pl.rel_l2(g, r) for g, r in zip(out[0], ref)) <= TOL
