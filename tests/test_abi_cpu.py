@@ -104,6 +104,9 @@ def test_null_arguments_are_einval(fdlib):
     assert fdlib._lib.fd_stream_create(0, None, None) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_stream_destroy(None) == fdlib.FD_EINVAL
     assert fdlib._lib.fd_set_time_fusion(None, 2) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_velocity_from_slowness(None, None, 4, None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_gradient_from_image(None, 1, None, None, 4, None) == fdlib.FD_EINVAL
+    assert fdlib._lib.fd_batch_create(None, 0, None) == fdlib.FD_EINVAL
 
 
 @pytest.mark.skipif(cuda_available(), reason="checks the no-device error path")
