@@ -7,6 +7,7 @@ error of 1e-4 (wavefield and traces); integer maps (source and receiver
 indices, sponge band extents) must match exactly.
 """
 import os
+import warnings
 
 import numpy as np
 import pytest
@@ -18,6 +19,10 @@ from conftest import cuda_available
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
 
 TOL = 1e-4
+
+
+class MeasuredErrors(UserWarning):
+    """The measured errors of a full-size comparison, reported in the test summary."""
 
 
 def gpu_run(fd, shot, nt, P0=None, Pold0=None):
@@ -471,10 +476,13 @@ def test_parity_3d_roofline_full_run(fdlib):
     e_P = digest.sketch_rel_l2(yP, ref["sketch_P"], float(ref["norm_P"]))
     e_O = digest.sketch_rel_l2(yO, ref["sketch_Pold"], float(ref["norm_Pold"]))
     e_T = digest.sketch_rel_l2(yT, ref["sketch_traces"], float(ref["norm_traces"]))
-    print(f"512^3 x 1000 vs oracle: plane {e_plane:.2e}, receiver row {e_row:.2e}; "
-          f"whole P {e_P:.2e}, Pold {e_O:.2e}, traces {e_T:.2e} (sketch estimates); "
-          f"norms {nP / float(ref['norm_P']) - 1:+.1e} {nO / float(ref['norm_Pold']) - 1:+.1e} "
-          f"{nT / float(ref['norm_traces']) - 1:+.1e}")
+    msg = (f"512^3 x 1000 vs oracle: plane {e_plane:.2e}, receiver row {e_row:.2e}; "
+           f"whole P {e_P:.2e}, Pold {e_O:.2e}, traces {e_T:.2e} (sketch estimates); "
+           f"norms {nP / float(ref['norm_P']) - 1:+.1e} {nO / float(ref['norm_Pold']) - 1:+.1e} "
+           f"{nT / float(ref['norm_traces']) - 1:+.1e}")
+    print(msg)
+    # also as a warning, so that the measured errors show in a quiet (-q) run's summary
+    warnings.warn(MeasuredErrors(msg))
     assert max(e_plane, e_row, e_P, e_O, e_T) <= TOL, (e_plane, e_row, e_P, e_O, e_T)
     for got, key in ((nP, "norm_P"), (nO, "norm_Pold"), (nT, "norm_traces")):
         assert abs(got / float(ref[key]) - 1.0) <= TOL, key
