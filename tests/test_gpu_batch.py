@@ -162,9 +162,11 @@ def test_stalled_item_times_out_and_context_survives(fdlib):
     assert_same(got, solo(fdlib, shots, [40, 40, 40]))
 
 
-def test_batched_workload_full_size_vs_oracle(fdlib, oracle):
+@pytest.mark.parametrize("tile", [0, 6])
+def test_batched_workload_full_size_vs_oracle(fdlib, oracle, tile):
     """The 64-shot batched workload at its full grid sizes, every shot started from a
-    random state so that every tile is active, 10 steps in one batch; six shots (the
+    random state so that every tile is active, 10 steps in one batch (the persistent
+    schedule, and the wide one with columns of 8 tiles); six shots (the
     smallest, the largest and four seeded others) against the oracle, rel L2 <= 1e-4
     for both levels and the traces."""
     nt = 10
@@ -176,6 +178,7 @@ def test_batched_workload_full_size_vs_oracle(fdlib, oracle):
             fdlib.fd_set_wavefield(m.handle, P0, Pm1, 0)
             fdlib.fd_set_trace_buffer(m.handle, None, nt)
         with fdlib.Batch(models) as b:
+            b.set_tuning(tile=tile, steps_per_launch=2000, ctas_per_sm=0, group_mb=96 if tile < 3 else 0)
             b.step(nt)
         sizes = [s.npoints for s in shots]
         pick = {int(np.argmin(sizes)), int(np.argmax(sizes))}
