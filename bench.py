@@ -322,6 +322,7 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
     batch.close()
     for m in models:
         m.close()
+    peak, _ = measured_hbm_peak()
     return {
         "workload": f"{nshots} 2D shots {min(shapes)}..{max(shapes)} (nz, nx), GRF velocity, sponge 20, {nt} steps",
         "updates": updates,
@@ -330,7 +331,8 @@ def measure_batched(nshots=64, nt=2000, repeats=1, tile=-1, group_mb=96):
         "plain_streams": {"streams": nstreams, "s": t_streams, "shots_per_s": nshots / t_streams,
                           "gupd": updates / t_streams / 1e9, "results_identical": bool(same_streams)},
         "batched": {"s": t_batch, "shots_per_s": nshots / t_batch, "gupd": updates / t_batch / 1e9,
-                    "launches": int(batch_launches), "tuning": tuning},
+                    "frac": 16 * updates / t_batch / 1e9 / peak, "launches": int(batch_launches),
+                    "tuning": tuning},
         "speedup": t_plain / t_batch,
         "speedup_vs_streams": t_streams / t_batch,
         "results_identical": bool(same),
@@ -389,11 +391,12 @@ def measure_batched_3d(nshots=24, nt=300, seed=6):
     batch.close()
     for m in models:
         m.close()
+    peak, _ = measured_hbm_peak()
     arm = lambda t: {"s": t, "shots_per_s": nshots / t, "gupd": updates / t / 1e9}
     return {"workload": f"{nshots} 3D shots, cubes {int(sizes.min())}..{int(sizes.max())}, {nt} steps, sponge 20",
             "plain": arm(t_plain), "plain_streams": dict(arm(t_streams), streams=8,
                                                          results_identical=bool(same_streams)),
-            "batched": arm(t_batch), "speedup": t_plain / t_batch, "speedup_vs_streams": t_streams / t_batch,
+            "batched": dict(arm(t_batch), frac=16 * updates / t_batch / 1e9 / peak), "speedup": t_plain / t_batch, "speedup_vs_streams": t_streams / t_batch,
             "results_identical": bool(same)}
 
 
