@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--adjoint-shots", type=int, default=8, help="adjoint workload: shots per gradient")
     ap.add_argument("--adjoint-lanes", type=int, default=4, help="adjoint workload: concurrent shot streams")
     ap.add_argument("--serve-shots", type=int, default=500, help="serving workload: requests in the stream")
-    ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "serving"])
+    ap.add_argument("--workload", default="roofline3d", choices=["roofline3d", "batched", "batched3d", "serving"])
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
     ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
     ap.add_argument("--batch-tile", type=int, default=-1,
@@ -809,6 +809,19 @@ def run_batched_line(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched3d_line(args, rank):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return
+    r = measure_batched_3d()
+    line = {"metric": "shots/s (batched 3D)", "value": r["batched"]["shots_per_s"], "unit": "shots/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": r["batched"]["s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving_line(args, rank):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -832,6 +845,8 @@ def main():
             run_reference(args, dist, rank, world)
         elif args.workload == "batched":
             run_batched_line(args, rank)
+        elif args.workload == "batched3d":
+            run_batched3d_line(args, rank)
         elif args.workload == "serving":
             run_serving_line(args, rank)
         else:
