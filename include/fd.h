@@ -374,7 +374,15 @@ fd_status fd_batch_step(fd_batch *b, int nsteps, const int *nsteps_each);
 fd_status fd_batch_set_fault(fd_batch *b, int stalled_item);
 /* Time every tuning candidate on trial_steps steps of this batch, keep the
  * fastest (cached per batch shape for the process) and write it to best.  The
- * trial steps change the models' state: call fd_reset or fd_run_shot after. */
+ * candidates are every schedule and tile shape, group budgets of 0, 24, 48 and
+ * 96 MB (those below the batch's footprint), and for the persistent schedules
+ * 0 or 2 CTAs per SM and trial_steps, trial_steps / 2, trial_steps / 4 and the
+ * current steps_per_launch (when shorter) steps per launch.  A trial cannot
+ * time a launch longer than itself: when trial_steps steps per launch wins and
+ * the current value is larger, the current value is kept (the wide schedules
+ * also keep it; they do not use it).  FD_EINVAL for trial_steps < 1.  The
+ * trial steps change the models' state: call fd_reset or fd_run_shot after.
+ * A 3D batch has nothing to tune and is left unchanged. */
 fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tuning *best);
 
 /* Allocation-free form of fd_batch_step.  The paper has no counterpart: it is

@@ -1131,7 +1131,8 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
             *best = b->tun;
         return FD_OK;
     }
-    const std::string sig = batch_signature(b) + "/" + std::to_string(trial_steps);
+    const std::string sig = batch_signature(b) + "/" + std::to_string(trial_steps) + "/" +
+                            std::to_string(b->tun.steps_per_launch);
     auto hit = g_tuning_cache.find(sig);
     if (hit != g_tuning_cache.end()) {
         fd_status st = fd_batch_set_tuning(b, &hit->second);
@@ -1146,7 +1147,13 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
     for (int g : {24, 48, 96})
         if (g < total_mb)
             groups.push_back(g);
+    // Steps per persistent launch: the trial length, half and a quarter of it,
+    // and the caller's value when shorter; each trial runs trial_steps steps.
     const int keep_k = b->tun.steps_per_launch;
+    std::vector<int> ks{trial_steps};
+    for (int k : {trial_steps / 2, trial_steps / 4, keep_k})
+        if (k >= 1 && k < trial_steps && std::find(ks.begin(), ks.end(), k) == ks.end())
+            ks.push_back(k);
     fd_batch_tuning best_t = b->tun;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -1154,31 +1161,36 @@ extern "C" fd_status fd_batch_autotune(fd_batch *b, int trial_steps, fd_batch_tu
     FD_CUDA(cudaEventCreate(&e1), "event");
     for (int tile = 0; tile < 8; ++tile)
         for (int g : groups)
-            for (int cps : {0, 2}) {
-                if (tile >= 3 && cps)
-                    continue;   // the wide schedule has no resident grid to size
-                fd_batch_tuning t{tile, trial_steps, cps, g};
-                fd_status st = fd_batch_set_tuning(b, &t);
-                if (!st)
-                    st = fd_batch_step(b, 1, nullptr);   // build, capture and warm up
-                if (st)
-                    continue;
-                cudaEventRecord(e0, b->stream);
-                st = fd_batch_step(b, trial_steps, nullptr);
-                cudaEventRecord(e1, b->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (!st && ms < best_ms) {
-                    best_ms = ms;
-                    best_t = t;
+            for (int cps : {0, 2})
+                for (int k : ks) {
+                    if (tile >= 3 && (cps || k != trial_steps))
+                        continue;   // the wide schedule has no resident grid and one launch per step
+                    fd_batch_tuning t{tile, k, cps, g};
+                    fd_status st = fd_batch_set_tuning(b, &t);
+                    if (!st)
+                        st = fd_batch_step(b, 1, nullptr);   // build, capture and warm up
+                    if (st)
+                        continue;
+                    cudaEventRecord(e0, b->stream);
+                    st = fd_batch_step(b, trial_steps, nullptr);
+                    cudaEventRecord(e1, b->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (!st && ms < best_ms) {
+                        best_ms = ms;
+                        best_t = t;
+                    }
                 }
-            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_ms >= 1e30f)
         return fail(FD_ECUDA, "fd_batch_autotune: no candidate ran");
-    best_t.steps_per_launch = keep_k;   // the trials time throughput; the caller's step granularity stays
+    // A trial cannot time launches longer than itself.  When the longest timed
+    // launch wins (or the wide schedule, where the value is unused), a caller's
+    // longer launch is kept: one launch boundary fewer per trial_steps steps.
+    if (best_t.tile >= 3 || (best_t.steps_per_launch == trial_steps && keep_k > trial_steps))
+        best_t.steps_per_launch = keep_k;
     g_tuning_cache[sig] = best_t;
     if (best)
         *best = best_t;
