@@ -18,7 +18,9 @@ velocity uploaded from pinned host memory and the traces read back every
 step), ``roofline`` (the step kernel's algorithmic HBM bytes per launch over
 its average launch time, against the measured copy bandwidth), ``clocks``
 (nvidia-smi sampled during the timed region) and ``cpu_baseline`` (the FP64
-oracle on the host cores, on a bounded sample of the same grid).
+oracle on the host cores, on a bounded sample of the same grid).  At N = 1 the
+line also carries the single-GPU sections: batched 2D and 3D shots, serving,
+the adjoint gradient, the paper's unfused routines and two-step fusion.
 """
 from __future__ import annotations
 
@@ -67,7 +69,8 @@ def parse_args():
     ap.add_argument("--shots", type=int, default=64, help="batched workload: number of 2D shots")
     ap.add_argument("--batch-nt", type=int, default=2000, help="batched workload: steps per shot")
     ap.add_argument("--batch-tile", type=int, default=-1,
-                    help="batched workload: tile variant (0: 64x16, 1: 64x32, 2: 128x16); -1 autotunes")
+                    help="batched workload: fd_batch_tuning.tile (0-2 persistent, 3-7 one launch per "
+                         "step); -1 autotunes")
     ap.add_argument("--group-mb", type=int, default=96, help="batched workload: group budget with --batch-tile")
     return ap.parse_args()
 
@@ -694,11 +697,14 @@ def run_b300(args, dist, rank, local, world):
     peak, peak_kind = measured_hbm_peak()
 
     fused = None
-    if rank == 0 and not args.skip_fused:
+    # the single-GPU sections run at N = 1 only: under torchrun they would hold
+    # every rank's GPU while rank 0 alone works
+    extras = rank == 0 and world == 1
+    if extras and not args.skip_fused:
         fused = measure_time_fusion(shot, model, stream, traces, args.steps)
 
     unfused = None
-    if rank == 0 and not args.skip_unfused:
+    if extras and not args.skip_unfused:
         unfused = measure_unfused(shot, model, stream)
 
     # ---- end to end: velocity up from pinned host memory, traces back, every step.
@@ -751,17 +757,17 @@ def run_b300(args, dist, rank, local, world):
                          f"{args.nt} time steps, FP64 oracle, {el:.1f} s"}
 
     batched = batched3 = None
-    if rank == 0 and not args.skip_batched:
+    if extras and not args.skip_batched:
         torch.cuda.empty_cache()
         batched = measure_batched(args.shots, args.batch_nt)
         batched3 = measure_batched_3d()
         batched["single_shot_2d_large"] = measure_2d_large()
     adj = None
-    if rank == 0 and not args.skip_adjoint:
+    if extras and not args.skip_adjoint:
         torch.cuda.empty_cache()
         adj = measure_adjoint(nshots=args.adjoint_shots, lanes=args.adjoint_lanes)
     served = None
-    if rank == 0 and not args.skip_serving:
+    if extras and not args.skip_serving:
         torch.cuda.empty_cache()
         served = measure_serving(args.serve_shots)
 
