@@ -349,10 +349,8 @@ def measure_batched_3d(nshots=24, nt=300, seed=6):
     over every model).  Results are compared bitwise."""
     import torch
     from paper_2311_05038_b300 import fd
-    rng = np.random.default_rng(seed)
-    sizes = rng.choice(np.array([128, 160, 192, 224, 256]), nshots)
-    vels = {int(n): wl.serving_3d_velocity(int(n), 5000 + int(n)) for n in set(sizes.tolist())}
-    shots = [wl.serving_3d_shot(i, int(n), nt, vel=vels[int(n)]) for i, n in enumerate(sizes)]
+    shots = wl.batched_3d_shots(nshots, nt, seed)
+    sizes = np.array([s.shape[0] for s in shots])
     updates = sum(s.npoints for s in shots) * nt
 
     def timed(fn):

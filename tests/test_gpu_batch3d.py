@@ -83,3 +83,24 @@ def test_batch3d_matches_the_oracle(fdlib, oracle):
         Pr, Por, trr = oracle.run(3, s.shape, s.h, s.dt, s.vel, sponge_width=s.sponge_width, src=s.src,
                                   wavelet=s.wavelet, receivers=s.receivers, nsteps=s.nt)
         assert max(pl.rel_l2(P, Pr), pl.rel_l2(Pold, Por), pl.rel_l2(tr, trr)) <= 1e-4
+
+
+def test_batched_3d_workload_full_size(fdlib, oracle):
+    """The batched 3D workload as the bench runs it (24 models, cubes 128-256, 300
+    steps, one batch, z chunks chosen for the whole launch): every model equals
+    its solo run bitwise, and the three 128^3 shots and one 160^3 shot match the
+    FP64 oracle over the whole run (final P, Pold and traces, rel L2 <= 1e-4)."""
+    shots = wl.batched_3d_shots()
+    nts = [s.nt for s in shots]
+    got = batched(fdlib, shots, nts)
+    assert_same(got, solo(fdlib, shots, nts))
+    picked = [i for i, s in enumerate(shots) if s.shape[0] == 128]
+    picked.append(next(i for i, s in enumerate(shots) if s.shape[0] == 160))
+    assert len(picked) == 4
+    for i in picked:
+        s = shots[i]
+        (P, Pold), tr = got[i]
+        Pr, Por, trr = oracle.run(3, s.shape, s.h, s.dt, s.vel, sponge_width=s.sponge_width, src=s.src,
+                                  wavelet=s.wavelet, receivers=s.receivers, nsteps=s.nt)
+        errs = (pl.rel_l2(P, Pr), pl.rel_l2(Pold, Por), pl.rel_l2(tr, trr))
+        assert np.all(np.isfinite(P)) and max(errs) <= 1e-4, (s.name, errs)

@@ -253,6 +253,16 @@ def serving_3d_shot(i: int, n: int, nt: int, seed: int = 4, sponge_width: int = 
                 name=f"3d-serve-{n}-{nt}-shot{i}")
 
 
+def batched_3d_shots(nshots: int = 24, nt: int = 300, seed: int = 6):
+    """The batched 3D workload: nshots cubes drawn from {128, ..., 256} (seed), each of
+    the serving mix (layered plus random velocity, one model per cube size, sponge 20,
+    the source position drawn per shot), nt steps each."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(np.array([128, 160, 192, 224, 256]), nshots)
+    vels = {int(n): serving_3d_velocity(int(n), 5000 + int(n)) for n in set(sizes.tolist())}
+    return [serving_3d_shot(i, int(n), nt, vel=vels[int(n)]) for i, n in enumerate(sizes)]
+
+
 def adjoint_3d(n: int = 256, nt: int = 1500, nshots: int = 8, seed: int = 5, sponge_width: int = 20):
     """The adjoint workload: smoothed random velocity in [1500, 4000] (GRF, 200 m),
     nshots surface shots at seeded positions, and the true model with a +5 %
