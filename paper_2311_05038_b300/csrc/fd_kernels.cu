@@ -219,6 +219,7 @@ __device__ __forceinline__ void step3d_body(const CUtensorMap &tmP, const CUtens
 
     const float2 M2 = make_float2(-6.0f, -6.0f);
     const float2 NEG1 = make_float2(-1.0f, -1.0f);
+    const float2 TWO = make_float2(2.0f, 2.0f);
     const float2 C1 = make_float2(prm.c1, prm.c1), C2 = make_float2(prm.c2, prm.c2);
     const float2 C3 = make_float2(prm.c3, prm.c3), C4 = make_float2(prm.c4, prm.c4);
     int sn = 4 % SP, phn = (4 / SP) & 1;   // P stage i+4
@@ -323,12 +324,13 @@ __device__ __forceinline__ void step3d_body(const CUtensorMap &tmP, const CUtens
             // sponge band: (w L'P + 2P - (1 - a) Pold) / (1 + a), scalar
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float2 p2 = half2of(pc, h), o2 = half2of(old, h), w2 = half2of(wv, h);
-                const float a0 = axv[2 * h] + ayz, a1 = axv[2 * h + 1] + ayz;
-                const float n0 = fmaf(w2.x, acc[h].x, fmaf(2.0f, p2.x, -(1.0f - a0) * o2.x));
-                const float n1 = fmaf(w2.y, acc[h].y, fmaf(2.0f, p2.y, -(1.0f - a1) * o2.y));
-                r[h] = make_float2(a0 != 0.0f ? __fdividef(n0, 1.0f + a0) : n0,
-                                   a1 != 0.0f ? __fdividef(n1, 1.0f + a1) : n1);
+                // per lane the scalar form's operations: a = ax + ayz, (a - 1) Pold = -(1 - a) Pold,
+                // fma(2, P, .), fma(w, L'P, .), then the division where a != 0
+                const float2 a2 = __fadd2_rn(make_float2(axv[2 * h], axv[2 * h + 1]), make_float2(ayz, ayz));
+                const float2 t2 = __fmul2_rn(__fadd2_rn(NEG1, a2), half2of(old, h));
+                const float2 n2 = __ffma2_rn(half2of(wv, h), acc[h], __ffma2_rn(TWO, half2of(pc, h), t2));
+                r[h] = make_float2(a2.x != 0.0f ? __fdividef(n2.x, 1.0f + a2.x) : n2.x,
+                                   a2.y != 0.0f ? __fdividef(n2.y, 1.0f + a2.y) : n2.y);
             }
         } else {
             // 2P - Pold as fma(-1, Pold, P + P): P + P is exact, one rounding as before
