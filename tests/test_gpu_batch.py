@@ -149,6 +149,14 @@ def test_autotune_steps_per_launch_candidates(fdlib):
         b.run_shots([50] * 3)
         got = [(m.wavefield(with_old=True), m.traces(50)) for m in models]
     assert_same(got, solo(fdlib, shots, [50] * 3))
+    # the same shapes from a longer starting launch are tuned afresh, not served
+    # from the cache entry above: a 12-step winner now keeps 2000
+    with fdlib.Batch(models) as b:
+        b.set_tuning(tile=0, steps_per_launch=2000, ctas_per_sm=0, group_mb=0)
+        best2 = b.autotune(trial_steps=12)
+        assert best2["steps_per_launch"] in ((2000, 6, 3) if best2["tile"] < 3 else (2000,))
+    for m in models:
+        m.close()
 
 
 def test_batch_rejects_a_mix_of_2d_and_3d_models(fdlib):
